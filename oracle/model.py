@@ -1,0 +1,291 @@
+"""The MujicΛ forward model and its hand-derived adjoint (gradient wrt s).
+
+Oracle (test infrastructure only).  FP64, single-threaded numpy.
+
+Forward model (Sec. 2.2.1 items 1-5, Sec. 2.2.2):
+  1. white noise s -> delta_L(k) = s(k) sqrt(P(|k|)/Delta^3), DC = 0
+     (Sec. 2.2.1 item 1, Eq. for delta_ic: the complex Gaussian modes are
+     built from real Gaussian variables s);
+  2. 2LPT displacement of the Lagrangian lattice to a_init, then n leapfrog
+     kick-drift-kick PM steps with FastPM factors to a = 1 (item 2);
+  3. plane-parallel redshift-space shift along one axis (item 3, Eq. RSD with
+     the line of sight fixed to a box axis);
+  4. galaxy bias: linear delta_g = b delta_m, or the power law + sigmoid of
+     Eq. galaxy_bias (item 4);
+  5. survey response lambda_obs = R lambda (item 5);
+  6. likelihood: Gaussian (1/2) sum R (b delta - d)^2 / sigma^2, or the
+     Poisson log-likelihood of Sec. 2.2.2 without the constant log N!;
+  plus the Gaussian prior (w/2) sum s^2 on the white noise.
+
+The gradient is the reverse-mode chain through every step above, written by
+hand: transposes of the spectral operators (conjugate multipliers), the CIC
+weight derivative, the reverse of each kick and drift.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import cosmology as cosmo
+from . import mesh as M
+
+
+@dataclass
+class Config:
+    n: int                      # mesh cells = particles per side
+    box: float                  # Mpc/h
+    omega_m: float = 0.25
+    a_init: float = 0.1
+    n_steps: int = 5
+    lpt_order: int = 2
+    rsd_axis: int = -1          # -1: none, 0..2: plane-parallel shift along that axis
+    likelihood: str = "gaussian"   # "gaussian" (linear bias) | "poisson" (power law + sigmoid)
+    bias_b: float = 1.5
+    sigma: float = 1.0
+    alpha: float = 0.7
+    delta_th: float = 1.2
+    K: float = 3.0
+    nbar_cell: float = 1.0
+    rho_floor: float = 1e-3
+    prior_weight: float = 1.0
+
+    @property
+    def cell(self):
+        return self.box / self.n
+
+
+def _sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def ic_amplitude(cfg, lnk, lnp):
+    """A(k) = sqrt(P(|k|) / Delta^3) on the half spectrum, A(0) = 0."""
+    k = np.sqrt(M.k_squared(cfg.n, cfg.box))
+    amp = np.sqrt(cosmo.power_from_table(k, lnk, lnp) / cfg.cell ** 3)
+    amp[0, 0, 0] = 0.0
+    return amp
+
+
+class _Ops:
+    """The spectral multipliers of the model, each defined once; the adjoint
+    applies their complex conjugates."""
+
+    def __init__(self, cfg, lnk, lnp):
+        n, box = cfg.n, cfg.box
+        self.amp = ic_amplitude(cfg, lnk, lnp)
+        self.ik2 = M.inv_k2(n, box)
+        self.d = [M.deriv(n, box, i) for i in range(3)]
+        # Psi1_i = -d_i phi1, lap phi1 = delta_L   ->  D_i / k^2 on delta_L
+        self.psi1 = [self.d[i] * self.ik2 * self.amp for i in range(3)]
+        # phi1_ij = d_i d_j phi1                   -> -D_i D_j / k^2 on delta_L
+        self.pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+        self.phi = {(i, j): -self.d[i] * self.d[j] * self.ik2 * self.amp for (i, j) in self.pairs}
+        # Psi2_i = +d_i phi2, lap phi2 = S          -> -D_i / k^2 on S
+        self.psi2 = [-self.d[i] * self.ik2 for i in range(3)]
+        # PM force F_i = -d_i phi, lap phi = 1.5 Om delta -> 1.5 Om D_i / k^2
+        self.force = [1.5 * cfg.omega_m * self.d[i] * self.ik2 for i in range(3)]
+
+
+def linear_field(s, cfg, lnk, lnp):
+    """delta_L in real space (Sec. 2.2.1 item 1)."""
+    ops = _Ops(cfg, lnk, lnp)
+    return M.irfft3(ops.amp * M.rfft3(s), cfg.n)
+
+
+def lpt(s, cfg, lnk, lnp, ops=None):
+    """2LPT (or Zel'dovich) displacement and momentum at a_init, (M,3) in Mpc/h.
+
+    x = q + D1 Psi1 + D2 Psi2,  p = a^3 E (D1' Psi1 + D2' Psi2),
+    S = sum_{i<j} (phi_ii phi_jj - phi_ij^2)  (Sec. 2.2.1 item 2: 2LPT to a=0.1)."""
+    ops = ops or _Ops(cfg, lnk, lnp)
+    n = cfg.n
+    sk = M.rfft3(np.asarray(s, dtype=np.float64))
+    psi1 = np.stack([M.irfft3(ops.psi1[i] * sk, n).reshape(-1) for i in range(3)], axis=1)
+    g = cosmo.growth([cfg.a_init], cfg.omega_m)
+    disp = g["D1"][0] * psi1
+    mom = g["Gp1"][0] * psi1
+    phi = None
+    psi2 = np.zeros_like(psi1)
+    if cfg.lpt_order == 2:
+        phi = {ij: M.irfft3(ops.phi[ij] * sk, n) for ij in ops.pairs}
+        src = (phi[(0, 0)] * phi[(1, 1)] + phi[(0, 0)] * phi[(2, 2)] + phi[(1, 1)] * phi[(2, 2)]
+               - phi[(0, 1)] ** 2 - phi[(0, 2)] ** 2 - phi[(1, 2)] ** 2)
+        srck = M.rfft3(src)
+        psi2 = np.stack([M.irfft3(ops.psi2[i] * srck, n).reshape(-1) for i in range(3)], axis=1)
+        disp = disp + g["D2"][0] * psi2
+        mom = mom + g["Gp2"][0] * psi2
+    return disp, mom, {"psi1": psi1, "psi2": psi2, "phi": phi, "growth": g}
+
+
+def positions_cells(disp, cfg):
+    """u = q/Delta + disp/Delta (cell units)."""
+    return M.lattice_cells(cfg.n) + disp / cfg.cell
+
+
+def force(disp, cfg, ops):
+    """PM force on every particle: CIC paint -> delta -> F_i = 1.5 Om D_i/k^2
+    delta(k) -> CIC readout.  Returns (F (M,3) in Mpc/h, Phi list of meshes,
+    delta mesh)."""
+    u = positions_cells(disp, cfg)
+    rho = M.cic_paint(u, cfg.n)
+    delta = rho - 1.0            # (N_mesh^3 / N_part^3) rho - 1 with N_mesh = N_part
+    dk = M.rfft3(delta)
+    phi = [M.irfft3(ops.force[i] * dk, cfg.n) for i in range(3)]
+    f = np.stack([M.cic_readout(u, phi[i]) for i in range(3)], axis=1)
+    return f, phi, delta
+
+
+def force_vjp(disp, fbar, cfg, ops):
+    """Transpose of the Jacobian of ``force`` (wrt disp) applied to fbar.
+
+    F_p,i = sum_c W(u_p - c) Phi_i(c),  Phi_i = G_i rho,  rho = sum_q W(u_q - c):
+      (A) readout weights: sum_i fbar_p,i sum_c dW/du (u_p - c) Phi_i(c)
+      (B) through rho: rhobar = sum_i G_i^T m_i, m_i = paint of fbar_i,
+          then sum_c dW/du (u_p - c) rhobar(c).
+    Result in 1/(Mpc/h) units of the cotangent (d/d disp = (1/Delta) d/du)."""
+    u = positions_cells(disp, cfg)
+    rho = M.cic_paint(u, cfg.n)
+    dk = M.rfft3(rho - 1.0)
+    phi = [M.irfft3(ops.force[i] * dk, cfg.n) for i in range(3)]
+    grad = np.zeros_like(disp)
+    for i in range(3):
+        grad += fbar[:, i:i + 1] * M.cic_readout_grad(u, phi[i])
+    rhobar = np.zeros((cfg.n,) * 3)
+    for i in range(3):
+        m_i = M.cic_paint(u, cfg.n, weights=fbar[:, i])
+        rhobar += M.irfft3(np.conj(ops.force[i]) * M.rfft3(m_i), cfg.n)
+    grad += M.cic_readout_grad(u, rhobar)
+    return grad / cfg.cell
+
+
+def evolve(s, cfg, lnk, lnp, keep=False):
+    """2LPT + leapfrog KDK to a = 1.  Returns (disp, mom, info); with keep=True
+    info["disp_k"] holds the displacement at each of the n+1 force
+    evaluations (for the adjoint)."""
+    ops = _Ops(cfg, lnk, lnp)
+    disp, mom, lpt_info = lpt(s, cfg, lnk, lnp, ops)
+    sch = cosmo.leapfrog_schedule(cfg.a_init, cfg.n_steps, cfg.omega_m)
+    f, _, _ = force(disp, cfg, ops)
+    disp_k = [disp.copy()] if keep else None
+    for k in range(cfg.n_steps):
+        mom = mom + sch["Ka"][k] * f
+        disp = disp + sch["Dr"][k] * mom
+        f, _, _ = force(disp, cfg, ops)
+        mom = mom + sch["Kb"][k] * f
+        if keep:
+            disp_k.append(disp.copy())
+    return disp, mom, {"ops": ops, "sched": sch, "disp_k": disp_k, "lpt": lpt_info}
+
+
+def rsd_coefficient(cfg):
+    """Comoving redshift-space shift per unit canonical momentum at a = 1:
+    v_pec / (a H) = p / (a^2 E(a)) (Sec. 2.2.1 item 3, Eq. RSD)."""
+    a = 1.0
+    return 1.0 / (a * a * float(cosmo.efunc(a, cfg.omega_m)))
+
+
+def observed_positions(disp, mom, cfg):
+    """Displacement after the plane-parallel RSD shift."""
+    out = disp.copy()
+    if cfg.rsd_axis >= 0:
+        out[:, cfg.rsd_axis] += rsd_coefficient(cfg) * mom[:, cfg.rsd_axis]
+    return out
+
+
+def final_density(disp_obs, cfg):
+    return M.cic_paint(positions_cells(disp_obs, cfg), cfg.n) - 1.0
+
+
+def _poisson_rate(delta, cfg):
+    """lambda / (R nbar) = max(1+delta, rho_floor)^alpha sigmoid(K (delta - delta_th))
+    (Eq. galaxy_bias with the floor that keeps the power law finite) and its
+    derivative wrt delta (zero below the floor for the power-law factor)."""
+    base = np.maximum(1.0 + delta, cfg.rho_floor)
+    sig = _sigmoid(cfg.K * (delta - cfg.delta_th))
+    g = base ** cfg.alpha * sig
+    dpow = np.where(1.0 + delta > cfg.rho_floor, cfg.alpha * base ** (cfg.alpha - 1.0), 0.0)
+    dg = dpow * sig + base ** cfg.alpha * cfg.K * sig * (1.0 - sig)
+    return g, dg
+
+
+def likelihood_terms(delta, data, resp, cfg):
+    """(-log L, d(-log L)/d delta) for the configured likelihood (Sec. 2.2.2)."""
+    if cfg.likelihood == "gaussian":
+        r = cfg.bias_b * delta - data
+        val = 0.5 * np.sum(resp * r * r) / cfg.sigma ** 2
+        grad = resp * cfg.bias_b * r / cfg.sigma ** 2
+        return val, grad
+    if cfg.likelihood == "poisson":
+        g, dg = _poisson_rate(delta, cfg)
+        mask = resp > 0
+        lam = np.where(mask, resp * cfg.nbar_cell * g, 1.0)
+        val = np.sum(np.where(mask, lam - data * np.log(lam), 0.0))
+        grad = np.where(mask, resp * cfg.nbar_cell * dg * (1.0 - data / lam), 0.0)
+        return val, grad
+    raise ValueError(cfg.likelihood)
+
+
+def loss(s, cfg, lnk, lnp, data, resp):
+    """Total loss = -log L + (w/2) sum s^2.  Returns (loss, parts dict)."""
+    disp, mom, _ = evolve(s, cfg, lnk, lnp)
+    delta = final_density(observed_positions(disp, mom, cfg), cfg)
+    lik, _ = likelihood_terms(delta, data, resp, cfg)
+    prior = 0.5 * cfg.prior_weight * float(np.sum(np.asarray(s, np.float64) ** 2))
+    return lik + prior, {"likelihood": lik, "prior": prior, "delta": delta,
+                         "disp": disp, "mom": mom}
+
+
+def gradient(s, cfg, lnk, lnp, data, resp, loss_weight=1.0, cot_delta=None):
+    """Value and gradient of loss_weight * loss + <cot_delta, delta_final> wrt s.
+
+    Reverse of the forward model, step by step:
+      likelihood -> final paint -> RSD -> for each leapfrog step in reverse:
+      second half-kick, drift, first half-kick -> 2LPT -> linear field;
+      plus the prior gradient."""
+    s = np.asarray(s, dtype=np.float64)
+    n = cfg.n
+    disp, mom, info = evolve(s, cfg, lnk, lnp, keep=True)
+    ops, sch, disp_k = info["ops"], info["sched"], info["disp_k"]
+    obs = observed_positions(disp, mom, cfg)
+    delta = final_density(obs, cfg)
+    lik, dlik = likelihood_terms(delta, data, resp, cfg)
+    prior = 0.5 * cfg.prior_weight * float(np.sum(s * s))
+    total = lik + prior
+
+    dbar = loss_weight * dlik
+    if cot_delta is not None:
+        dbar = dbar + cot_delta
+    # final paint: delta = paint(u_obs) - 1
+    xbar = M.cic_readout_grad(positions_cells(obs, cfg), dbar) / cfg.cell
+    pbar = np.zeros_like(xbar)
+    if cfg.rsd_axis >= 0:
+        pbar[:, cfg.rsd_axis] += rsd_coefficient(cfg) * xbar[:, cfg.rsd_axis]
+    # leapfrog steps in reverse
+    for k in range(cfg.n_steps - 1, -1, -1):
+        xbar = xbar + force_vjp(disp_k[k + 1], sch["Kb"][k] * pbar, cfg, ops)
+        pbar = pbar + sch["Dr"][k] * xbar
+        xbar = xbar + force_vjp(disp_k[k], sch["Ka"][k] * pbar, cfg, ops)
+    # 2LPT:  disp = D1 Psi1 + D2 Psi2,  mom = Gp1 Psi1 + Gp2 Psi2
+    g = info["lpt"]["growth"]
+    psi1bar = g["D1"][0] * xbar + g["Gp1"][0] * pbar
+    sbar_k = np.zeros_like(ops.amp, dtype=np.complex128)
+    for i in range(3):
+        sbar_k += np.conj(ops.psi1[i]) * M.rfft3(psi1bar[:, i].reshape(n, n, n))
+    if cfg.lpt_order == 2:
+        psi2bar = g["D2"][0] * xbar + g["Gp2"][0] * pbar
+        srcbar = np.zeros((n, n, n))
+        for i in range(3):
+            srcbar += M.irfft3(np.conj(ops.psi2[i]) * M.rfft3(psi2bar[:, i].reshape(n, n, n)), n)
+        phi = info["lpt"]["phi"]
+        phibar = {
+            (0, 0): srcbar * (phi[(1, 1)] + phi[(2, 2)]),
+            (1, 1): srcbar * (phi[(0, 0)] + phi[(2, 2)]),
+            (2, 2): srcbar * (phi[(0, 0)] + phi[(1, 1)]),
+            (0, 1): -2.0 * srcbar * phi[(0, 1)],
+            (0, 2): -2.0 * srcbar * phi[(0, 2)],
+            (1, 2): -2.0 * srcbar * phi[(1, 2)],
+        }
+        for ij in ops.pairs:
+            sbar_k += np.conj(ops.phi[ij]) * M.rfft3(phibar[ij])
+    grad = M.irfft3(sbar_k, n) + loss_weight * cfg.prior_weight * s
+    return total, grad, {"likelihood": lik, "prior": prior, "delta": delta,
+                         "disp": disp, "mom": mom}
