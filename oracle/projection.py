@@ -112,8 +112,19 @@ def fourier_modes(n, box, n_bins=N_BINS, k_min=K_MIN):
     plane = (iz == 0) | (iz == n // 2)
     canonical = np.where(plane, flat < partner, True)
     kmag = np.sqrt(M.k_squared(n, box))
-    kmax = np.sqrt(3.0) * np.pi * n / box
-    binid = np.minimum((kmag / kmax * n_bins).astype(np.int64), n_bins - 1)
+    # floor(|k| / (sqrt(3) k_Nyq) * n_bins) with |k| = 2 pi |m| / L for the
+    # integer mode vector m: the largest b with 3 n^2 b^2 <= 4 n_bins^2 |m|^2,
+    # evaluated in integers so that modes exactly on a bin edge are binned
+    # without rounding
+    mx = np.where(ix < n // 2, ix, ix - n).astype(np.int64)
+    my = np.where(iy < n // 2, iy, iy - n).astype(np.int64)
+    m2 = mx * mx + my * my + iz.astype(np.int64) ** 2
+    lhs = 4 * n_bins * n_bins * m2
+    c = 3 * n * n
+    binid = np.floor(np.sqrt(lhs / c)).astype(np.int64)
+    binid = np.where(c * binid * binid > lhs, binid - 1, binid)
+    binid = np.where(c * (binid + 1) ** 2 <= lhs, binid + 1, binid)
+    binid = np.minimum(binid, n_bins - 1)
     sel = canonical & (kmag >= k_min)
     idx = flat[sel]
     order = np.argsort(idx)

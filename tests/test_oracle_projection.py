@@ -179,3 +179,26 @@ def test_composite_order():
     step = P.rom_real(step, resp, tr)
     step, _ = P.project(step, 3, 4)
     np.testing.assert_array_equal(out, step)
+
+
+def test_fourier_bins_exact_on_edges():
+    # m = (32, 32, 32) at n = 256 lies exactly on the edge between bins 24
+    # and 25: |m| / (sqrt(3) n / 2) * 100 = 25
+    n, box = 256, 500.0
+    idx, b, _ = P.fourier_modes(n, box)
+    h = n // 2 + 1
+    flat = (32 * n + 32) * h + 32
+    assert b[np.searchsorted(idx, flat)] == 25
+    # and the bin of every mode agrees with a brute-force exact rational test
+    rng = np.random.default_rng(0)
+    pick = rng.choice(idx.size, 2000, replace=False)
+    for q in pick:
+        f = idx[q]
+        ix, iy, iz = f // (n * h), (f // h) % n, f % h
+        mx = ix if ix < n // 2 else ix - n
+        my = iy if iy < n // 2 else iy - n
+        m2 = mx * mx + my * my + iz * iz
+        bb = 0
+        while 3 * n * n * (bb + 1) ** 2 <= 4 * 100 * 100 * m2:
+            bb += 1
+        assert b[q] == min(bb, 99)
