@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Gradient evaluations per second of the MujicΛ hot path on one GB300.
+
+Workload: the masked-reconstruction configuration -- 256^3 mesh and
+particles, 500 Mpc/h box, 2LPT to a = 0.1 then 10 leapfrog steps to a = 1,
+power-law + sigmoid bias (0.7, 1.2, 3.0) with a survey response R (40 deg
+cone, radial n(r) ~ r^2 exp(-(r/300)^1.5), 16x16 angular completeness
+patches U(0.3, 0.9)), Poisson likelihood on mock counts drawn at
+nbar = 1e-3 (h/Mpc)^3, Gaussian prior, m = 10 L-BFGS.
+
+One step = one augmented L-BFGS iteration of the hot path: lbfgs_step
+(pair push + two-loop direction), the trial point s + eps p_hat (eps =
+min(|d|, 1)), project_rank_match (projection every step; Fourier and
+real-space rank-order matching on every 20th step, the paper's schedule),
+and pm_adjoint (forward model + gradient) at the trial point.  Each step is
+exactly one gradient evaluation, so steps/s = gradient evals/s.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PM fwd+adjoint gradient evals/s at 256^3 (FP32 mesh/FFT/particles, FP64 reductions)"
+UNIT = "gradient evals/s"
+N, BOX, STEPS_PM = 256, 500.0, 10
+NBAR = 1e-3
+ROM_EVERY = 20
+
+def mock_inputs(api, inputs, plan1_cfg, lnk, lnp, rank):
+    """Selection R, mock counts N_G ~ Poisson(lambda(s_true)) and the start s0."""
+    import torch
+    dev = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+    R = inputs.survey_selection(N, BOX, seed=4)
+    s_true = inputs.white_noise(N, 1 + 1000 * rank)
+    # normalisation: nbar_cell = nbar Delta^3 / mean_box[(1+delta)^alpha sigmoid(...)]
+    probe = api.Plan(plan1_cfg, lnk, lnp)
+    ones = dev(np.ones((N, N, N), np.float32))
+    g = api.pm_expected_counts(probe, dev(s_true), ones)
+    mean_g = float(g.cpu().numpy().astype(np.float64).mean())
+    del probe, g, ones
+    torch.cuda.empty_cache()
+    nbar_cell = NBAR * (BOX / N) ** 3 / mean_g
+    return R, s_true, nbar_cell
+
+
+def config(api, nbar_cell, precision="f32"):
+    return api.Config(n=N, box=BOX, n_steps=STEPS_PM, lpt_order=2, rsd_axis=-1, likelihood="poisson",
+                      precision=precision, alpha=0.7, delta_th=1.2, K=3.0, nbar_cell=nbar_cell,
+                      rho_floor=1e-3, prior_weight=1.0)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_sample(n_small=64):
+    """One FP64 oracle gradient of the same physics at n_small^3 (same cell
+    size), seconds; scaled to 256^3 by the cell count."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import cosmology as OC
+    from oracle import model as OM
+    from paper_2604_26823_gb300 import inputs
+    box = BOX * n_small / N
+    lnk, lnp = OC.linear_power_table()
+    cfg = OM.Config(n=n_small, box=box, n_steps=STEPS_PM, lpt_order=2, likelihood="poisson",
+                    nbar_cell=NBAR * (BOX / N) ** 3, alpha=0.7, delta_th=1.2, K=3.0, prior_weight=1.0)
+    s = inputs.white_noise(n_small, 2).astype(np.float64)
+    resp = inputs.survey_selection(n_small, box, 4, observer=(box / 2, box / 2, -0.3 * box),
+                                   r_scale=300.0 * n_small / N).astype(np.float64)
+    counts = inputs.poisson_counts(resp * NBAR * (BOX / N) ** 3, 3).astype(np.float64)
+    OC.growth([0.1], 0.25)  # warm the growth cache outside the timing
+    t0 = time.perf_counter()
+    OM.gradient(s, cfg, lnk, lnp, counts, resp)
+    return time.perf_counter() - t0, (N / n_small) ** 3
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    n_small = 32
+    for _ in range(args.warmup):
+        oracle_sample(n_small)
+    times = []
+    for _ in range(args.steps):
+        t, scale = oracle_sample(n_small)
+        times.append(t * scale)
+    per = float(np.mean(times))
+    value = 1.0 / per
+    sample = (f"one FP64 oracle gradient (2LPT + 10 steps, Poisson, same cell size) at {n_small}^3 per step, "
+              f"time scaled x{int((N / n_small) ** 3)} by cell count to 256^3")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "masked-recon-256", "n_mesh": N, "n_particles": N ** 3, "box": BOX,
+                       "pm_steps": STEPS_PM, "parallelism": f"replicas x{args.gpus}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2604_26823_gb300 import api, build, inputs
+    build.build()
+    lib = api.L.load()
+    torch.cuda.set_device(local)
+    lnk, lnp = api.pm_linear_power_table()
+    dev = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+
+    R_h, s_true, nbar_cell = mock_inputs(api, inputs, config(api, 1.0), lnk, lnp, rank)
+    cfg = config(api, nbar_cell)
+    plan = api.Plan(cfg, lnk, lnp)
+    R = dev(R_h)
+    lam = api.pm_expected_counts(plan, dev(s_true), R)
+    counts_h = inputs.poisson_counts(lam.cpu().numpy(), 3 + 1000 * rank)
+    counts = dev(counts_h)
+    del lam
+    n_gal = float(counts_h.sum())
+    vol_frac = float((R_h > 0).mean())
+    ncount = api.pm_count_positive(plan, R)
+    t_real = dev(inputs.sorted_normal_targets(ncount, 7))
+    t_four = dev(inputs.sorted_normal_targets_per_bin(api.pm_rom_fourier_counts(plan), 8))
+    st = api.LBFGS(N ** 3, m=10, precision="f32")
+    s0 = inputs.white_noise(N, 2 + 1000 * rank)
+    state = {"s": dev(s0), "g": torch.empty((N, N, N), dtype=torch.float32, device="cuda"),
+             "trial": torch.empty((N, N, N), dtype=torch.float32, device="cuda"), "it": 0}
+    _, state["g"] = api.pm_adjoint(plan, state["s"], counts, R, grad_out=state["g"])
+
+    def step(plan_, st_, S, cnt, resp, tr, tf):
+        it = S["it"]
+        d, gd, dn, _ = api.lbfgs_step(st_, S["s"], S["g"])
+        eps = min(dn, 1.0)
+        api.pm_axpy(eps / dn, d, S["s"], out=S["trial"])
+        mode = api.L.PM_PROJECT | (api.L.PM_ROM_FOURIER | api.L.PM_ROM_REAL if it % ROM_EVERY == 0 else 0)
+        api.project_rank_match(plan_, S["trial"], mode, R=resp, targets_real=tr, targets_fourier=tf, seed=6,
+                               counter=it)
+        loss, _ = api.pm_adjoint(plan_, S["trial"], cnt, resp, grad_out=S["g"])
+        S["s"], S["trial"] = S["trial"], S["s"]
+        S["it"] = it + 1
+        return loss
+
+    for _ in range(args.warmup):
+        step(plan, st, state, counts, R, t_real, t_four)
+    state["it"] = 0
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = Clocks(local)
+    api.pm_profile(plan, True, 200000)
+    launches0 = lib.pm_launch_count()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    losses = []
+    for _ in range(args.steps):
+        losses.append(step(plan, st, state, counts, R, t_real, t_four))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.pm_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = {c: api.pm_profile_read(plan, c) for c in api.PROFILE_CLASSES}
+    api.pm_profile(plan, False)
+    barrier(ws)
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * args.steps / (ms_max / 1e3)
+
+    # dominant kernel class: algorithmic bytes (recorded per launch by the
+    # library) over its event-timed duration, against the measured HBM peak
+    peak, peak_src = 6800.0, "fallback"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, peak_src = float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    classes = {k: {"ms_total": v[0], "launches": v[1], "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] else None}
+               for k, v in prof.items()}
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n, dom_b = prof[dom]
+    roof = None
+    if dom_n:
+        achieved = dom_b / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src, "launches": dom_n,
+                "mean_launch_ms": dom_ms / dom_n, "algorithmic_bytes_per_launch": dom_b / dom_n,
+                "share_of_step": dom_ms / ms}
+    # FP64 path: same workload and schedule
+    fp64 = None
+    if not args.no_fp64:
+        del plan
+        torch.cuda.empty_cache()
+        plan64 = api.Plan(config(api, nbar_cell, "f64"), lnk, lnp)
+        d64 = lambda x: torch.as_tensor(x).to(device="cuda", dtype=torch.float64)
+        st64 = api.LBFGS(N ** 3, m=10, precision="f64")
+        S64 = {"s": d64(s0), "g": torch.empty((N, N, N), dtype=torch.float64, device="cuda"),
+               "trial": torch.empty((N, N, N), dtype=torch.float64, device="cuda"), "it": 0}
+        c64, R64 = d64(counts_h), d64(R_h)
+        tr64, tf64 = d64(t_real.cpu().numpy()), d64(t_four.cpu().numpy())
+        _, S64["g"] = api.pm_adjoint(plan64, S64["s"], c64, R64, grad_out=S64["g"])
+        step(plan64, st64, S64, c64, R64, tr64, tf64)
+        S64["it"] = 0
+        torch.cuda.synchronize()
+        k64 = max(2, min(args.steps, 4))
+        t0 = time.perf_counter()
+        for _ in range(k64):
+            step(plan64, st64, S64, c64, R64, tr64, tf64)
+        torch.cuda.synchronize()
+        fp64 = {"value": k64 / (time.perf_counter() - t0), "unit": UNIT, "steps": k64}
+        del plan64, st64, S64
+        torch.cuda.empty_cache()
+        plan = api.Plan(cfg, lnk, lnp)
+
+    # end to end through the public API with pinned host buffers: every step
+    # uploads s, the counts and R and reads back the loss
+    s_pin = torch.from_numpy(state["s"].cpu().numpy()).pin_memory()
+    c_pin = torch.from_numpy(counts_h).pin_memory()
+    r_pin = torch.from_numpy(R_h).pin_memory()
+    S2 = {"s": torch.empty_like(state["s"]), "g": torch.empty_like(state["g"]),
+          "trial": torch.empty_like(state["s"]), "it": 1}
+    cnt2, R2 = torch.empty_like(counts), torch.empty_like(R)
+    st2 = api.LBFGS(N ** 3, m=10, precision="f32")
+    S2["s"].copy_(s_pin, non_blocking=True)
+    cnt2.copy_(c_pin, non_blocking=True)
+    R2.copy_(r_pin, non_blocking=True)
+    _, S2["g"] = api.pm_adjoint(plan, S2["s"], cnt2, R2, grad_out=S2["g"])
+    torch.cuda.synchronize()
+    k_e2e = args.steps
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        S2["s"].copy_(s_pin, non_blocking=True)
+        cnt2.copy_(c_pin, non_blocking=True)
+        R2.copy_(r_pin, non_blocking=True)
+        step(plan, st2, S2, cnt2, R2, t_real, t_four)   # returns the loss on the host
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e_t = max_over_ranks(e2e_t, ws)
+    e2e = {"value": ws * k_e2e / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * N ** 3,
+           "d2h_bytes_per_step": 8}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        t, scale = oracle_sample(64)
+        cpu = {"value": 1.0 / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 oracle gradient (same physics and cell size) at 64^3 took {t:.1f} s, "
+                         f"scaled x{int(scale)} by cell count to 256^3"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "masked-recon-256", "n_mesh": N, "n_particles": N ** 3, "box": BOX,
+                           "pm_steps": STEPS_PM, "lbfgs_m": 10, "rom_every": ROM_EVERY,
+                           "likelihood": "poisson", "galaxies": n_gal, "selection_volume_frac": vol_frac,
+                           "parallelism": f"replicas x{ws}", "l2": "working set ~7 GB >> 129 MB L2 (no flush)"},
+                "fp64_path": fp64, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+                "gpu_launches": int(launches), "clocks": clk, "kernel_classes": classes,
+                "final_loss": losses[-1]}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = (1, 0, 0) if args.impl == "reference" and int(os.environ.get("WORLD_SIZE", "1")) == 1 \
+        else dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * mujica_pm.h -- C ABI of the GB300 particle-mesh forward model, its adjoint,
+ * the projected L-BFGS step and the projection / rank-order-matching
+ * operator of MujicΛ ("Initial Condition Reconstruction on Realistic Redshift
+ * Surveys with Augmented Optimization").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns a pm_status (0 = PM_OK) and never throws.  On an
+ *   error, pm_last_error() returns a message for the calling host thread.
+ * - Meshes and the white-noise parameter s are caller-owned DEVICE buffers,
+ *   contiguous, C order [n][n][n] (x slowest, z fastest), of the plan's
+ *   element type: float for PM_PREC_F32, double for PM_PREC_F64.
+ * - Particle arrays are SoA [3][n^3] of the same type; particle
+ *   p = (i*n + j)*n + l starts at the Lagrangian node (i, j, l) * L / n.
+ * - The library allocates no device memory: each object reports the size of
+ *   the device workspace it needs and the caller passes that workspace in.
+ *   The host-side plan / state objects are small malloc'ed structs.
+ * - Calls are asynchronous on the given cudaStream_t (pass 0 for the legacy
+ *   default stream) except those that return a host scalar (loss, dot
+ *   products, counts): those synchronise that stream before returning.
+ * - Units: comoving Mpc/h, wavenumbers h/Mpc, H0 = 1, momentum
+ *   p = a^3 E(a) dx/da.
+ * - Citations are to sections and equations of the paper.
+ */
+#ifndef MUJICA_PM_H
+#define MUJICA_PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pm_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  PM_OK = 0,
+  PM_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum value */
+  PM_ERR_UNSUPPORTED = 2,   /* mesh not a power of two in [16, 512], bad option combination */
+  PM_ERR_CUDA = 3,          /* a CUDA runtime call failed; message has the CUDA error string */
+  PM_ERR_NONFINITE = 4,     /* NaN / Inf in an input or in the evaluated loss */
+  PM_ERR_WORKSPACE = 5,     /* workspace too small or misaligned (256-byte alignment required) */
+  PM_ERR_LINESEARCH = 6,    /* reserved for the reconstruction driver: line search exhausted */
+  PM_ERR_DEVICE_STATUS = 7  /* a kernel reported an internal inconsistency */
+} pm_status;
+
+typedef enum { PM_PREC_F32 = 0, PM_PREC_F64 = 1 } pm_precision;
+typedef enum { PM_LIK_GAUSSIAN = 0, PM_LIK_POISSON = 1 } pm_likelihood;
+
+/* Model configuration (Sec. 2.2.1 items 1-5, Sec. 2.2.2). */
+typedef struct {
+  int32_t n;                /* mesh cells per side = particles per side; power of two, 16..512 */
+  int32_t n_steps;          /* leapfrog steps, uniform in a from a_init to 1 (Sec. 2.2.1 item 2); >= 1 */
+  int32_t lpt_order;        /* 1 (Zel'dovich) or 2 (2LPT, the paper's choice) */
+  int32_t rsd_axis;         /* -1: no redshift-space shift; 0, 1, 2: plane-parallel shift along x, y, z */
+  int32_t likelihood;       /* PM_LIK_GAUSSIAN: linear bias b, 1/2 sum R (b delta - d)^2 / sigma^2
+                               PM_LIK_POISSON: Eq. galaxy_bias with R and the Poisson likelihood of Sec. 2.2.2 */
+  int32_t precision;        /* PM_PREC_F32 (FP32 mesh / FFT / particles, FP64 reductions) or PM_PREC_F64 */
+  int32_t checkpoint_every; /* 0: pm_adjoint keeps every step's particle state; c > 0: keeps (x, p)
+                               every c steps and recomputes the steps in between (same result) */
+  int32_t reserved0;
+  double box;               /* side of the periodic box, Mpc/h */
+  double omega_m;           /* flat LCDM matter density (E(a) and the Poisson source) */
+  double a_init;            /* scale factor of the 2LPT initial condition, 0 < a_init < 1 */
+  double bias_b;            /* Gaussian: linear bias b */
+  double sigma;             /* Gaussian: noise standard deviation per cell */
+  double alpha;             /* Poisson: power-law index (paper: 0.7) */
+  double delta_th;          /* Poisson: sigmoid threshold (paper: 1.2) */
+  double K;                 /* Poisson: sigmoid steepness (paper: 3.0) */
+  double nbar_cell;         /* Poisson: normalisation N_G of Eq. galaxy_bias, galaxies per cell */
+  double rho_floor;         /* Poisson: floor on 1 + delta inside the power law (1e-3) */
+  double prior_weight;      /* weight w of the Gaussian prior (w/2) sum s^2; 0 = likelihood only */
+} pm_config;
+
+typedef struct pm_plan pm_plan;
+typedef struct lbfgs_state lbfgs_state;
+
+/* Message describing the last error on this host thread ("" if none). */
+const char *pm_last_error(void);
+/* Library version string. */
+const char *pm_version(void);
+/* Number of CUDA kernel launches this library has issued since it was loaded
+ * (all plans and threads; diagnostics, no counterpart in the paper). */
+int64_t pm_launch_count(void);
+
+/* ---- host-side coefficients (no GPU) ----------------------------------- */
+
+/* Linear matter power spectrum at z = 0 (Sec. 2.2.1 item 1: P_k of the fiducial
+ * cosmology): Eisenstein & Hu (1998) no-wiggle transfer function, spectral
+ * index n_s, normalised to sigma8 with an 8 Mpc/h top hat.  Writes n_k
+ * log-spaced points k in [k_min, k_max] (h/Mpc) as (ln k, ln P) into the host
+ * arrays lnk, lnp.  Errors: PM_ERR_INVALID_ARG. */
+pm_status pm_linear_power_table(double omega_m, double omega_b, double h, double sigma8,
+                                double n_s, double k_min, double k_max, int32_t n_k,
+                                double *lnk, double *lnp);
+
+/* Growth factors of flat LCDM at n_a scale factors (host arrays): linear D1
+ * (D1(1) = 1), second order D2 (-3/7 D1^2 in the EdS limit) and the momentum
+ * growth Gp1 = a^3 E dD1/da, Gp2 = a^3 E dD2/da used by 2LPT and the FastPM
+ * kick / drift factors (Sec. 2.2.1 item 2).  Any output may be NULL. */
+pm_status pm_growth(double omega_m, int32_t n_a, const double *a, double *D1, double *D2,
+                    double *Gp1, double *Gp2);
+
+/* ---- plan: the forward model and its adjoint --------------------------- */
+
+/* Device workspace bytes a plan with this configuration needs. */
+pm_status pm_workspace_bytes(const pm_config *cfg, size_t *bytes);
+
+/* Create a plan.  lnk / lnp: host table (n_pk >= 2 points, ln k increasing) of
+ * the linear power spectrum, interpolated linearly in (ln k, ln P) and clamped
+ * at its ends.  workspace: caller-owned device buffer of at least
+ * pm_workspace_bytes() bytes, 256-byte aligned, that must outlive the plan;
+ * it is not cleared by the caller.  Synchronous (uploads tables).  Errors:
+ * PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED, PM_ERR_WORKSPACE, PM_ERR_CUDA. */
+pm_status pm_plan_create(const pm_config *cfg, const double *lnk, const double *lnp, int32_t n_pk,
+                         void *workspace, size_t bytes, pm_plan **out);
+pm_status pm_plan_destroy(pm_plan *plan);
+
+/* Forward model and loss (Sec. 2.2.1 items 1-5, Sec. 2.2.2, plus the prior):
+ *   loss = -log L(data | delta(s)) + (w/2) sum s^2
+ * s: white noise [n^3]; data: Gaussian d or Poisson counts N_G [n^3]; R: survey
+ * response [n^3] (Gaussian: per-cell weight; Poisson: cells with R > 0 enter
+ * the likelihood).  loss_out: host double.  delta_out (nullable): final
+ * matter density contrast after the redshift-space shift, [n^3].
+ * Synchronises the stream.  Errors: PM_ERR_INVALID_ARG, PM_ERR_NONFINITE (loss
+ * not finite), PM_ERR_CUDA. */
+pm_status pm_forward(pm_plan *plan, const void *s, const void *data, const void *R,
+                     double *loss_out, void *delta_out, pm_stream_t stream);
+
+/* Vector-Jacobian product of loss_weight * loss + <cot_delta, delta> with
+ * respect to s (the gradient the L-BFGS iterations of Sec. 2.3.1 consume),
+ * by the hand-derived reverse of every stage.  cot_delta (nullable): [n^3].
+ * grad_out: [n^3].  loss_out (nullable): host double, the loss (unweighted).
+ * Synchronises the stream.  Errors: as pm_forward. */
+pm_status pm_adjoint(pm_plan *plan, const void *s, const void *data, const void *R,
+                     double loss_weight, const void *cot_delta, double *loss_out,
+                     void *grad_out, pm_stream_t stream);
+
+/* Likelihood and prior parts of the last loss this plan evaluated. */
+pm_status pm_last_terms(const pm_plan *plan, double *likelihood, double *prior);
+
+/* ---- stage probes (same kernels as the forward model) ------------------ */
+
+/* delta_L = IFFT[ sqrt(P(|k|)/Delta^3) FFT[s] ], DC = 0 (Sec. 2.2.1 item 1). */
+pm_status pm_linear_field(pm_plan *plan, const void *s, void *delta_l_out, pm_stream_t stream);
+/* 2LPT displacement (Mpc/h) and momentum at a_init (Sec. 2.2.1 item 2), SoA [3][n^3]. */
+pm_status pm_lpt(pm_plan *plan, const void *s, void *disp_out, void *mom_out, pm_stream_t stream);
+/* PM force F = -grad phi, lap phi = 1.5 Omega_m delta, read out at the particles
+ * displaced by disp (Mpc/h, SoA), SoA [3][n^3] output; density_out (nullable)
+ * receives delta = rho - 1 painted from disp. */
+pm_status pm_force(pm_plan *plan, const void *disp, void *force_out, void *density_out,
+                   pm_stream_t stream);
+/* Displacement and momentum at a = 1 after 2LPT and the leapfrog steps. */
+pm_status pm_evolve(pm_plan *plan, const void *s, void *disp_out, void *mom_out, pm_stream_t stream);
+
+/* Model mean per cell at s, the rate the mock galaxies are drawn from:
+ * Poisson: lambda = R nbar (1+delta)^alpha sigmoid(K (delta - delta_th)) (Eq.
+ * galaxy_bias times the survey response of Sec. 2.2.1 item 5); Gaussian:
+ * b delta.  out: [n^3]. */
+pm_status pm_expected_counts(pm_plan *plan, const void *s, const void *R, void *out, pm_stream_t stream);
+
+/* ---- kernel timing (no counterpart in the paper; diagnostics) ----------
+ * pm_profile(plan, 1, capacity) creates 2*capacity CUDA events and from then
+ * on brackets every launch of the profiled kernel classes on its stream
+ * (up to capacity launches); pm_profile(plan, 0, 0) stops recording.
+ * pm_profile_read sums, over the recorded launches of one class, the elapsed
+ * time, the launch count and the algorithmic bytes each launch must move
+ * (its inputs read once and outputs written once) (synchronises).
+ * Classes: 0 fused readout+kick+drift+paint, 1 z-pass r2c, 2 column pass,
+ * 3 x-pass with multipliers, 4 z-pass c2r, 5 adjoint 3-channel paint,
+ * 6 adjoint gather, 7 likelihood. */
+pm_status pm_profile(pm_plan *plan, int32_t enable, int32_t capacity);
+pm_status pm_profile_read(pm_plan *plan, int32_t kernel_class, double *ms_total, int64_t *launches,
+                          double *bytes_total);
+
+/* ---- projection and rank-order matching (Sec. 2.3.1, Sec. 2.3.2) ------- */
+
+#define PM_PROJECT 1u       /* z-score, then reset |s_hat| > 10 to counter-based N(0,1) draws */
+#define PM_ROM_FOURIER 2u   /* rank-order matching of Fourier modes in 100 |k| bins, k >= 0.1 h/Mpc */
+#define PM_ROM_REAL 4u      /* rank-order matching of s over the cells with R > 0 */
+
+/* Number of values Fourier matching touches in each of the 100 bins (host
+ * int64[100]); the caller draws that many sorted N(0,1) targets per bin. */
+pm_status pm_rom_fourier_counts(const pm_plan *plan, int64_t *counts_out);
+/* Number of cells with R > 0 (synchronises). */
+pm_status pm_count_positive(pm_plan *plan, const void *R, int64_t *count_out, pm_stream_t stream);
+
+/* Applies, in this order and each only when its bit is in mode: Fourier
+ * matching, real-space matching, projection.  s_inout [n^3] in place.
+ * targets_real: device [count of R > 0], sorted descending (plan type);
+ * targets_fourier: device, the per-bin target lists concatenated in bin
+ * order, each sorted descending (plan type).  Ranks break ties by index
+ * (lower index = larger).  rng_seed / rng_counter key the reset draws.
+ * n_reset_out (nullable host): number of reset values; when non-NULL the call
+ * synchronises.  Errors: PM_ERR_INVALID_ARG, PM_ERR_NONFINITE (NaN in s),
+ * PM_ERR_CUDA. */
+pm_status project_rank_match(pm_plan *plan, void *s_inout, uint32_t mode, const void *R,
+                             const void *targets_real, const void *targets_fourier,
+                             uint64_t rng_seed, uint64_t rng_counter, int64_t *n_reset_out,
+                             pm_stream_t stream);
+
+/* ---- L-BFGS (Sec. 2.3.1) ------------------------------------------------ */
+
+pm_status lbfgs_workspace_bytes(int64_t n_elems, int32_t m, int32_t precision, size_t *bytes);
+pm_status lbfgs_create(int64_t n_elems, int32_t m, int32_t precision, void *workspace,
+                       size_t bytes, lbfgs_state **out);
+pm_status lbfgs_destroy(lbfgs_state *st);
+/* Forget the stored pairs and the previous point. */
+pm_status lbfgs_reset(lbfgs_state *st);
+/* If a previous point exists, store the pair (x_new - x_prev, g_new - g_prev)
+ * when s.y > 1e-10 |s| |y|; then d_out = -H g_new by the two-loop recursion
+ * with H0 = gamma I (gamma = s.y / y.y of the newest pair, 1 without pairs);
+ * if g.d >= 0 the pairs are dropped and d = -g.  Host outputs (nullable):
+ * gdotd_out = g.d, dnorm_out = |d|, pushed_out = whether a pair was stored.
+ * Dot products accumulate in FP64.  Synchronises. */
+pm_status lbfgs_step(lbfgs_state *st, const void *x_new, const void *g_new, void *d_out,
+                     double *gdotd_out, double *dnorm_out, int32_t *pushed_out,
+                     pm_stream_t stream);
+
+/* out = y + alpha * x over n elements of the given precision (device). */
+pm_status pm_axpy(int64_t n, int32_t precision, double alpha, const void *x, const void *y,
+                  void *out, pm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUJICA_PM_H */

@@ -1,0 +1,322 @@
+"""Python binding of the GB300 particle-mesh library (argument marshalling).
+
+Every numerical step runs in the CUDA kernels behind the C ABI; PyTorch only
+provides device memory (tensors, workspaces) and streams.  The functions keep
+the C names (``pm_forward``, ``pm_adjoint``, ``lbfgs_step``,
+``project_rank_match``, ...) and take ``Plan`` / ``LBFGS`` objects and CUDA
+tensors.
+"""
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype, numel, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor with {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Config:
+    """Mirror of ``pm_config`` (Sec. 2.2.1 / 2.2.2 parameters)."""
+    n: int
+    box: float
+    n_steps: int = 10
+    lpt_order: int = 2
+    rsd_axis: int = -1
+    likelihood: str = "gaussian"      # "gaussian" | "poisson"
+    precision: str = "f32"            # "f32" | "f64"
+    checkpoint_every: int = 0
+    omega_m: float = 0.25
+    a_init: float = 0.1
+    bias_b: float = 1.5
+    sigma: float = 1.0
+    alpha: float = 0.7
+    delta_th: float = 1.2
+    K: float = 3.0
+    nbar_cell: float = 1.0
+    rho_floor: float = 1e-3
+    prior_weight: float = 1.0
+
+    def to_c(self):
+        c = L.pm_config()
+        c.n, c.n_steps, c.lpt_order, c.rsd_axis = self.n, self.n_steps, self.lpt_order, self.rsd_axis
+        c.likelihood = {"gaussian": L.PM_LIK_GAUSSIAN, "poisson": L.PM_LIK_POISSON}[self.likelihood]
+        c.precision = {"f32": L.PM_PREC_F32, "f64": L.PM_PREC_F64}[self.precision]
+        c.checkpoint_every = self.checkpoint_every
+        for f in ("box", "omega_m", "a_init", "bias_b", "sigma", "alpha", "delta_th", "K",
+                  "nbar_cell", "rho_floor", "prior_weight"):
+            setattr(c, f, float(getattr(self, f)))
+        return c
+
+    @property
+    def dtype(self):
+        return torch.float32 if self.precision == "f32" else torch.float64
+
+
+def pm_linear_power_table(omega_m=0.25, omega_b=0.045, h=0.73, sigma8=0.9, n_s=1.0,
+                          k_min=1e-4, k_max=1e2, n_k=512):
+    """Host table (ln k, ln P) of the no-wiggle LCDM P(k) (library host code)."""
+    lib = L.load()
+    lnk = np.zeros(n_k)
+    lnp = np.zeros(n_k)
+    L.check(lib.pm_linear_power_table(omega_m, omega_b, h, sigma8, n_s, k_min, k_max, n_k,
+                                      lnk.ctypes.data_as(L._DP), lnp.ctypes.data_as(L._DP)),
+            "pm_linear_power_table")
+    return lnk, lnp
+
+
+def pm_growth(omega_m, a):
+    lib = L.load()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = [np.zeros_like(a) for _ in range(4)]
+    L.check(lib.pm_growth(omega_m, a.size, a.ctypes.data_as(L._DP),
+                          *[o.ctypes.data_as(L._DP) for o in out]), "pm_growth")
+    return dict(zip(("D1", "D2", "Gp1", "Gp2"), out))
+
+
+class Plan:
+    """A pm_plan plus its device workspace (a torch uint8 tensor)."""
+
+    def __init__(self, config: Config, lnk=None, lnp=None, device="cuda"):
+        lib = L.load()
+        self.config = config
+        self.cfg = config.to_c()
+        self.n = config.n
+        self.ncell = config.n ** 3
+        self.dtype = config.dtype
+        if lnk is None:
+            lnk, lnp = pm_linear_power_table(omega_m=config.omega_m)
+        lnk = np.ascontiguousarray(lnk, dtype=np.float64)
+        lnp = np.ascontiguousarray(lnp, dtype=np.float64)
+        nbytes = ctypes.c_size_t()
+        L.check(lib.pm_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)), "pm_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+        h = ctypes.c_void_p()
+        L.check(lib.pm_plan_create(ctypes.byref(self.cfg), lnk.ctypes.data_as(L._DP),
+                                   lnp.ctypes.data_as(L._DP), lnk.size,
+                                   ctypes.c_void_p(self.workspace.data_ptr()), self.workspace_bytes,
+                                   ctypes.byref(h)), "pm_plan_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.load().pm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def mesh(self, t, name):
+        return _ptr(t, self.dtype, self.ncell, name)
+
+    def parts(self, t, name):
+        return _ptr(t, self.dtype, 3 * self.ncell, name)
+
+    def empty(self, *shape):
+        return torch.empty(shape or (self.n, self.n, self.n), dtype=self.dtype, device="cuda")
+
+
+def pm_forward(plan, s, data, R, delta_out=None, stream=None):
+    """loss = -log L + (w/2) sum s^2; optionally the final density contrast."""
+    loss = ctypes.c_double()
+    L.check(L.load().pm_forward(plan.handle, plan.mesh(s, "s"), plan.mesh(data, "data"), plan.mesh(R, "R"),
+                                ctypes.byref(loss), plan.mesh(delta_out, "delta_out"), _stream(stream)),
+            "pm_forward")
+    return loss.value
+
+
+def pm_adjoint(plan, s, data, R, loss_weight=1.0, cot_delta=None, grad_out=None, stream=None):
+    """(loss, gradient of loss_weight * loss + <cot_delta, delta> wrt s)."""
+    if grad_out is None:
+        grad_out = torch.empty_like(s)
+    loss = ctypes.c_double()
+    L.check(L.load().pm_adjoint(plan.handle, plan.mesh(s, "s"), plan.mesh(data, "data"), plan.mesh(R, "R"),
+                                float(loss_weight), plan.mesh(cot_delta, "cot_delta"), ctypes.byref(loss),
+                                plan.mesh(grad_out, "grad_out"), _stream(stream)), "pm_adjoint")
+    return loss.value, grad_out
+
+
+def pm_last_terms(plan):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    L.check(L.load().pm_last_terms(plan.handle, ctypes.byref(a), ctypes.byref(b)), "pm_last_terms")
+    return a.value, b.value
+
+
+def pm_linear_field(plan, s, out=None, stream=None):
+    out = plan.empty() if out is None else out
+    L.check(L.load().pm_linear_field(plan.handle, plan.mesh(s, "s"), plan.mesh(out, "out"), _stream(stream)),
+            "pm_linear_field")
+    return out
+
+
+def pm_lpt(plan, s, stream=None):
+    disp, mom = plan.empty(3, plan.ncell), plan.empty(3, plan.ncell)
+    L.check(L.load().pm_lpt(plan.handle, plan.mesh(s, "s"), plan.parts(disp, "disp"), plan.parts(mom, "mom"),
+                            _stream(stream)), "pm_lpt")
+    return disp, mom
+
+
+def pm_force(plan, disp, with_density=False, stream=None):
+    force = plan.empty(3, plan.ncell)
+    dens = plan.empty() if with_density else None
+    L.check(L.load().pm_force(plan.handle, plan.parts(disp, "disp"), plan.parts(force, "force"),
+                              plan.mesh(dens, "density"), _stream(stream)), "pm_force")
+    return (force, dens) if with_density else force
+
+
+def pm_evolve(plan, s, stream=None):
+    disp, mom = plan.empty(3, plan.ncell), plan.empty(3, plan.ncell)
+    L.check(L.load().pm_evolve(plan.handle, plan.mesh(s, "s"), plan.parts(disp, "disp"), plan.parts(mom, "mom"),
+                               _stream(stream)), "pm_evolve")
+    return disp, mom
+
+
+def pm_expected_counts(plan, s, R, out=None, stream=None):
+    """Model mean per cell (Poisson rate or b delta) at s."""
+    out = plan.empty() if out is None else out
+    L.check(L.load().pm_expected_counts(plan.handle, plan.mesh(s, "s"), plan.mesh(R, "R"), plan.mesh(out, "out"),
+                                        _stream(stream)), "pm_expected_counts")
+    return out
+
+
+PROFILE_CLASSES = {"kdk": 0, "z_r2c": 1, "col": 2, "x_fused": 3, "z_c2r": 4, "adj_paint": 5,
+                   "adj_gather": 6, "loss": 7}
+
+
+def pm_profile(plan, enable=True, capacity=20000):
+    L.check(L.load().pm_profile(plan.handle, 1 if enable else 0, capacity if enable else 0), "pm_profile")
+
+
+def pm_profile_read(plan, kernel_class):
+    """(total milliseconds, launches, algorithmic bytes) of one kernel class
+    since pm_profile."""
+    c = PROFILE_CLASSES.get(kernel_class, kernel_class)
+    ms, k, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    L.check(L.load().pm_profile_read(plan.handle, int(c), ctypes.byref(ms), ctypes.byref(k), ctypes.byref(b)),
+            "pm_profile_read")
+    return ms.value, k.value, b.value
+
+
+def pm_rom_fourier_counts(plan):
+    out = np.zeros(100, dtype=np.int64)
+    L.check(L.load().pm_rom_fourier_counts(plan.handle, out.ctypes.data_as(L._I64P)), "pm_rom_fourier_counts")
+    return out
+
+
+def pm_count_positive(plan, R, stream=None):
+    c = ctypes.c_int64()
+    L.check(L.load().pm_count_positive(plan.handle, plan.mesh(R, "R"), ctypes.byref(c), _stream(stream)),
+            "pm_count_positive")
+    return c.value
+
+
+def project_rank_match(plan, s_inout, mode, R=None, targets_real=None, targets_fourier=None, seed=0,
+                       counter=0, stream=None):
+    """In place: Fourier matching, real-space matching, projection (by mode bits).
+    Returns the number of reset values."""
+    nres = ctypes.c_int64()
+    tr = None
+    if targets_real is not None:
+        tr = _ptr(targets_real, plan.dtype, targets_real.numel(), "targets_real")
+    tf = None
+    if targets_fourier is not None:
+        tf = _ptr(targets_fourier, plan.dtype, targets_fourier.numel(), "targets_fourier")
+    L.check(L.load().project_rank_match(plan.handle, plan.mesh(s_inout, "s"), int(mode),
+                                        plan.mesh(R, "R") if R is not None else None, tr, tf,
+                                        int(seed), int(counter), ctypes.byref(nres), _stream(stream)),
+            "project_rank_match")
+    return nres.value
+
+
+class LBFGS:
+    """lbfgs_state plus its device workspace."""
+
+    def __init__(self, n_elems, m=10, precision="f32", device="cuda"):
+        lib = L.load()
+        self.n = int(n_elems)
+        self.prec = {"f32": L.PM_PREC_F32, "f64": L.PM_PREC_F64}[precision]
+        self.dtype = torch.float32 if precision == "f32" else torch.float64
+        nb = ctypes.c_size_t()
+        L.check(lib.lbfgs_workspace_bytes(self.n, m, self.prec, ctypes.byref(nb)), "lbfgs_workspace_bytes")
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=device)
+        h = ctypes.c_void_p()
+        L.check(lib.lbfgs_create(self.n, m, self.prec, ctypes.c_void_p(self.workspace.data_ptr()), nb.value,
+                                 ctypes.byref(h)), "lbfgs_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.load().lbfgs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbfgs_reset(state):
+    L.check(L.load().lbfgs_reset(state.handle), "lbfgs_reset")
+
+
+def lbfgs_step(state, x_new, g_new, d_out=None, stream=None):
+    """Push the pair from the previous point, then d = -H g.  Returns
+    (d, g.d, |d|, pushed)."""
+    if d_out is None:
+        d_out = torch.empty_like(g_new)
+    gd, dn, pushed = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    L.check(L.load().lbfgs_step(state.handle, _ptr(x_new, state.dtype, state.n, "x_new"),
+                                _ptr(g_new, state.dtype, state.n, "g_new"), _ptr(d_out, state.dtype, state.n, "d"),
+                                ctypes.byref(gd), ctypes.byref(dn), ctypes.byref(pushed), _stream(stream)),
+            "lbfgs_step")
+    return d_out, gd.value, dn.value, bool(pushed.value)
+
+
+def pm_axpy(alpha, x, y, out=None, stream=None):
+    """out = y + alpha x (device kernel)."""
+    if out is None:
+        out = torch.empty_like(y)
+    prec = L.PM_PREC_F32 if y.dtype == torch.float32 else L.PM_PREC_F64
+    n = y.numel()
+    L.check(L.load().pm_axpy(n, prec, float(alpha), _ptr(x, y.dtype, n, "x"), _ptr(y, y.dtype, n, "y"),
+                             _ptr(out, y.dtype, n, "out"), _stream(stream)), "pm_axpy")
+    return out
+
+
+class PMLoss(torch.autograd.Function):
+    """loss(s) as an autograd node: forward runs pm_adjoint and caches the
+    gradient, backward scales it by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, s, plan, data, R):
+        loss, grad = pm_adjoint(plan, s.detach().contiguous(), data, R)
+        ctx.save_for_backward(grad)
+        return torch.tensor(loss, dtype=torch.float64, device=s.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (grad,) = ctx.saved_tensors
+        w = float(gout)
+        # gout * grad = grad + (gout - 1) grad, by the library's axpy kernel
+        out = grad if w == 1.0 else pm_axpy(w - 1.0, grad, grad)
+        return out, None, None, None

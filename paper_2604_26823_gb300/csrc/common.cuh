@@ -1,0 +1,173 @@
+// Shared device types and helpers of the particle-mesh library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdio>
+#include <string>
+
+namespace pm {
+
+// ---- complex / vector types per precision -------------------------------
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+template <typename T> using cx = typename Cx<T>::type;
+
+// four-component force mesh element (F_x, F_y, F_z, unused)
+template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
+
+template <typename C> __host__ __device__ __forceinline__ C mkc(decltype(C::x) r, decltype(C::x) i) {
+  C c;
+  c.x = r;
+  c.y = i;
+  return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mkc<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mkc<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mkc<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mkc<C>(a.x, -a.y); }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return mkc<C>(a.x * s, a.y * s); }
+// multiply by +i (SIGN > 0) or -i (SIGN < 0)
+template <int SIGN, typename C> __device__ __forceinline__ C cmul_i(C a) {
+  return SIGN > 0 ? mkc<C>(-a.y, a.x) : mkc<C>(a.y, -a.x);
+}
+
+// ---- fixed-point deposition ---------------------------------------------
+// CIC deposits are accumulated as 64-bit integers, q = rint(w * 2^E), with
+// integer atomics: integer addition is associative, so the painted mesh is
+// identical for every thread schedule (deterministic deposition).
+__device__ __forceinline__ void fx_add(unsigned long long *p, long long q) {
+  atomicAdd(p, (unsigned long long)q);
+}
+
+// ---- launch geometry ----------------------------------------------------
+constexpr int kSMs = 152;
+
+inline int grid_for(int64_t n, int threads, int max_blocks = 1 << 30) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+// Number of kernel launches the library has issued since it was loaded
+// (every launch site calls note_launch() right before its launch).
+inline std::atomic<long long> g_launches{0};
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// thread-local error string of the C ABI
+void set_error(const std::string &msg);
+
+// Optional CUDA-event timing of kernel classes (off by default): every
+// launch of a profiled class is bracketed by two events on its stream.
+enum ProfClass : int {
+  P_KDK = 0,       // fused readout + kick + drift + paint
+  P_Z_R2C = 1,     // z pass real -> half complex
+  P_COL = 2,       // strided complex column pass (y, or plain x)
+  P_X_FUSED = 3,   // x pass with spectral multipliers
+  P_Z_C2R = 4,     // z pass half complex -> real
+  P_ADJ_PAINT = 5, // 3-channel cotangent paint
+  P_ADJ_GATHER = 6,// adjoint weight-derivative gather
+  P_LOSS = 7,      // likelihood / reductions
+  P_OTHER = 8,     // 2LPT pointwise, memsets, ROM, projection
+  P_NCLASS = 9
+};
+
+struct Profiler {
+  bool on = false;
+  int used = 0, cap = 0;
+  cudaEvent_t *ev = nullptr;  // 2 per launch
+  int *cls = nullptr;
+  double *bytes = nullptr;    // algorithmic bytes of each launch
+  ~Profiler() { release(); }
+  void release() {
+    for (int i = 0; i < 2 * cap; ++i) cudaEventDestroy(ev[i]);
+    delete[] ev;
+    delete[] cls;
+    delete[] bytes;
+    ev = nullptr;
+    cls = nullptr;
+    bytes = nullptr;
+    cap = used = 0;
+    on = false;
+  }
+  cudaError_t enable(int capacity) {
+    release();
+    ev = new cudaEvent_t[2 * capacity];
+    cls = new int[capacity];
+    bytes = new double[capacity];
+    for (int i = 0; i < 2 * capacity; ++i) {
+      const cudaError_t e = cudaEventCreate(&ev[i]);
+      if (e != cudaSuccess) {
+        cap = i / 2;
+        return e;
+      }
+    }
+    cap = capacity;
+    on = true;
+    return cudaSuccess;
+  }
+  int begin(int c, cudaStream_t st, double nbytes) {
+    if (!on || used >= cap) return -1;
+    cls[used] = c;
+    bytes[used] = nbytes;
+    cudaEventRecord(ev[2 * used], st);
+    return used++;
+  }
+  void end(int slot, cudaStream_t st) {
+    if (slot >= 0) cudaEventRecord(ev[2 * slot + 1], st);
+  }
+  // total milliseconds, launch count and algorithmic bytes of one class (synchronises)
+  cudaError_t read(int c, double *ms, int64_t *count, double *nbytes) {
+    double t = 0.0, b = 0.0;
+    int64_t k = 0;
+    for (int i = 0; i < used; ++i) {
+      if (cls[i] != c) continue;
+      cudaError_t e = cudaEventSynchronize(ev[2 * i + 1]);
+      if (e != cudaSuccess) return e;
+      float f = 0.f;
+      e = cudaEventElapsedTime(&f, ev[2 * i], ev[2 * i + 1]);
+      if (e != cudaSuccess) return e;
+      t += f;
+      b += bytes[i];
+      ++k;
+    }
+    *ms = t;
+    *count = k;
+    *nbytes = b;
+    return cudaSuccess;
+  }
+};
+
+// RAII bracket of one profiled launch
+struct ProfScope {
+  Profiler &p;
+  cudaStream_t st;
+  int slot;
+  ProfScope(Profiler &pr, int c, cudaStream_t s, double nbytes) : p(pr), st(s), slot(pr.begin(c, s, nbytes)) {}
+  ~ProfScope() { p.end(slot, st); }
+};
+
+}  // namespace pm
+
+#define PM_CUDA_TRY(expr)                                                              \
+  do {                                                                                 \
+    cudaError_t e__ = (expr);                                                          \
+    if (e__ != cudaSuccess) {                                                          \
+      ::pm::set_error(std::string(#expr) + ": " + cudaGetErrorString(e__));            \
+      return PM_ERR_CUDA;                                                              \
+    }                                                                                  \
+  } while (0)
+
+#define PM_LAUNCH_CHECK()                                                              \
+  do {                                                                                 \
+    cudaError_t e__ = cudaGetLastError();                                              \
+    if (e__ != cudaSuccess) {                                                          \
+      ::pm::set_error(std::string("kernel launch: ") + cudaGetErrorString(e__));      \
+      return PM_ERR_CUDA;                                                              \
+    }                                                                                  \
+  } while (0)

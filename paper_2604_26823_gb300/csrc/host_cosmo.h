@@ -1,0 +1,28 @@
+// Host FP64 cosmology coefficients used to build a plan (no GPU code).
+#pragma once
+#include <array>
+#include <vector>
+
+namespace pmhost {
+
+struct GrowthPoint {
+  double D1, D2, Gp1, Gp2;  // growth factors and a^3 E dD/da
+};
+
+struct Schedule {
+  std::vector<double> a;   // n_steps + 1 scale factors
+  std::vector<double> Ka;  // first half-kick factor of step k
+  std::vector<double> Kb;  // second half-kick factor of step k
+  std::vector<double> Dr;  // drift factor of step k
+  GrowthPoint lpt;         // growth at a_init
+  double e_final;          // E(a = 1)
+};
+
+double efunc(double a, double om);
+void growth(double om, int n, const double *a, GrowthPoint *out);
+Schedule leapfrog(double om, double a_init, int n_steps);
+double eh98_nowiggle(double k, double om, double ob, double h, double tcmb);
+void power_table(double om, double ob, double h, double sigma8, double ns, double kmin, double kmax,
+                 int nk, double *lnk, double *lnp);
+
+}  // namespace pmhost

@@ -1,0 +1,352 @@
+// Per-particle kernels of the PM model: cloud-in-cell deposition (paint),
+// interpolation (readout), the leapfrog kick / drift, the redshift-space
+// shift, and the adjoint gathers with CIC weight derivatives.
+//
+// Particle p = (i*N + j)*N + l carries its displacement d from the Lagrangian
+// node (i, j, l) in cell units (FP32 or FP64).  The cell of a particle is
+// formed in integers, c = (node + floor(d)) mod N, with the FP offset
+// f = d - floor(d) in [0, 1), so large boxes keep sub-cell accuracy.
+// CIC: node c + o (o in {0,1}^3) gets prod_a (o_a ? f_a : 1 - f_a); the weight
+// derivative is prod over the other axes times (o_a ? +1 : -1).
+// Sec. 2.2.1 item 2 (PM steps), item 3 (RSD), Sec. 2.2.2 (CiC binning).
+#pragma once
+#include "common.cuh"
+
+namespace pm {
+namespace part {
+
+struct Lattice {
+  int logn;
+  int mask;
+  __device__ __forceinline__ void node(int64_t p, int &i, int &j, int &l) const {
+    i = (int)(p >> (2 * logn));
+    j = (int)(p >> logn) & mask;
+    l = (int)p & mask;
+  }
+};
+
+template <typename T> struct Cell {
+  int c[3];   // base node (periodic)
+  T f[3];     // fractional offset in [0, 1)
+};
+
+template <typename T>
+__device__ __forceinline__ Cell<T> locate(const Lattice &L, int64_t p, T dx, T dy, T dz) {
+  int nd[3];
+  L.node(p, nd[0], nd[1], nd[2]);
+  const T d[3] = {dx, dy, dz};
+  Cell<T> c;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T fl = floor(d[a]);
+    c.f[a] = d[a] - fl;
+    c.c[a] = (nd[a] + (int)fl) & L.mask;
+  }
+  return c;
+}
+
+__device__ __forceinline__ int64_t mesh_index(const Lattice &L, int x, int y, int z) {
+  return ((((int64_t)x) << L.logn | y) << L.logn) | z;
+}
+
+// Deposit weight v (already scaled by 2^E) onto the 8 nodes, integer atomics.
+template <typename T>
+__device__ __forceinline__ void deposit(const Lattice &L, unsigned long long *mesh, const Cell<T> &c, T v) {
+  const int x1 = (c.c[0] + 1) & L.mask, y1 = (c.c[1] + 1) & L.mask, z1 = (c.c[2] + 1) & L.mask;
+  const T wx[2] = {T(1) - c.f[0], c.f[0]};
+  const T wy[2] = {T(1) - c.f[1], c.f[1]};
+  const T wz[2] = {T(1) - c.f[2], c.f[2]};
+  const int xs[2] = {c.c[0], x1}, ys[2] = {c.c[1], y1}, zs[2] = {c.c[2], z1};
+#pragma unroll
+  for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const T wxy = wx[ox] * wy[oy] * v;
+#pragma unroll
+      for (int oz = 0; oz < 2; ++oz) {
+        const T w = wxy * wz[oz];
+        long long q;
+        if constexpr (sizeof(T) == 4) q = __float2ll_rn(w);
+        else q = __double2ll_rn(w);
+        if (q) fx_add(mesh + mesh_index(L, xs[ox], ys[oy], zs[oz]), q);
+      }
+    }
+}
+
+// F = sum_c W(u - c) Phi(c) over a 4-component mesh (x, y, z used).
+template <typename T>
+__device__ __forceinline__ void readout3(const Lattice &L, const V4<T> *__restrict__ phi, const Cell<T> &c,
+                                         T &fx, T &fy, T &fz) {
+  const int x1 = (c.c[0] + 1) & L.mask, y1 = (c.c[1] + 1) & L.mask, z1 = (c.c[2] + 1) & L.mask;
+  const T wx[2] = {T(1) - c.f[0], c.f[0]};
+  const T wy[2] = {T(1) - c.f[1], c.f[1]};
+  const T wz[2] = {T(1) - c.f[2], c.f[2]};
+  const int xs[2] = {c.c[0], x1}, ys[2] = {c.c[1], y1}, zs[2] = {c.c[2], z1};
+  fx = fy = fz = T(0);
+#pragma unroll
+  for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) {
+      const T wxy = wx[ox] * wy[oy];
+#pragma unroll
+      for (int oz = 0; oz < 2; ++oz) {
+        const V4<T> m = phi[mesh_index(L, xs[ox], ys[oy], zs[oz])];
+        const T w = wxy * wz[oz];
+        fx += w * m.x;
+        fy += w * m.y;
+        fz += w * m.z;
+      }
+    }
+}
+
+// Gradient wrt u of sum_c W(u - c) [a . Phi(c) + s(c)] (adjoint gather);
+// phi may be null (then only the scalar mesh s contributes).
+template <typename T>
+__device__ __forceinline__ void grad_gather(const Lattice &L, const V4<T> *__restrict__ phi,
+                                            const T *__restrict__ smesh, const Cell<T> &c, T ax, T ay,
+                                            T az, T &gx, T &gy, T &gz) {
+  const int x1 = (c.c[0] + 1) & L.mask, y1 = (c.c[1] + 1) & L.mask, z1 = (c.c[2] + 1) & L.mask;
+  const T wx[2] = {T(1) - c.f[0], c.f[0]};
+  const T wy[2] = {T(1) - c.f[1], c.f[1]};
+  const T wz[2] = {T(1) - c.f[2], c.f[2]};
+  const T sg[2] = {T(-1), T(1)};
+  const int xs[2] = {c.c[0], x1}, ys[2] = {c.c[1], y1}, zs[2] = {c.c[2], z1};
+  gx = gy = gz = T(0);
+#pragma unroll
+  for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int oz = 0; oz < 2; ++oz) {
+        const int64_t idx = mesh_index(L, xs[ox], ys[oy], zs[oz]);
+        T val = smesh ? smesh[idx] : T(0);
+        if (phi) {
+          const V4<T> m = phi[idx];
+          val += ax * m.x + ay * m.y + az * m.z;
+        }
+        gx += sg[ox] * wy[oy] * wz[oz] * val;
+        gy += wx[ox] * sg[oy] * wz[oz] * val;
+        gz += wx[ox] * wy[oy] * sg[oz] * val;
+      }
+}
+
+template <typename T> __device__ __forceinline__ void atomic_max_abs(unsigned long long *slot, T v) {
+  // |v| of a float / double orders like its bit pattern (non-negative)
+  if constexpr (sizeof(T) == 4) {
+    atomicMax(reinterpret_cast<unsigned int *>(slot), __float_as_uint(fabsf(v)));
+  } else {
+    atomicMax(slot, (unsigned long long)__double_as_longlong(fabs(v)));
+  }
+}
+
+template <typename T> __device__ __forceinline__ T read_max_abs(const unsigned long long *slot) {
+  if constexpr (sizeof(T) == 4) return __uint_as_float(*reinterpret_cast<const unsigned int *>(slot));
+  else return __longlong_as_double((long long)*slot);
+}
+
+// Exponent E with 2^E * maxabs * n_particles < 2^61 (no overflow of the
+// int64 accumulators); deposits are rint(w * 2^E).
+__device__ __forceinline__ int fixed_exponent(double maxabs, int log2_particles) {
+  if (!(maxabs > 0.0)) return 0;
+  int e;
+  frexp(maxabs, &e);  // maxabs < 2^e
+  return 61 - log2_particles - e;
+}
+
+// ---- kernels ------------------------------------------------------------
+
+struct Geo {
+  Lattice L;
+  int64_t np;        // particles
+  int log2np;
+};
+
+// disp = (D1 psi1 + D2 psi2)/Delta, mom = (Gp1 psi1 + Gp2 psi2)/Delta (cell units),
+// then paint disp into the fixed-point density.
+template <typename T>
+__global__ void k_lpt_init(Geo g, const T *__restrict__ psi1, const T *__restrict__ psi2, T d1, T d2,
+                           T gp1, T gp2, T *__restrict__ disp, T *__restrict__ mom,
+                           unsigned long long *rho, const int *fx_exp, int use_psi2) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.np) return;
+  T d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T a1 = psi1[a * g.np + p];
+    const T a2 = use_psi2 ? psi2[a * g.np + p] : T(0);
+    d[a] = d1 * a1 + d2 * a2;
+    disp[a * g.np + p] = d[a];
+    mom[a * g.np + p] = gp1 * a1 + gp2 * a2;
+  }
+  if (rho) {
+    const Cell<T> c = locate<T>(g.L, p, d[0], d[1], d[2]);
+    deposit<T>(g.L, rho, c, (T)ldexp(1.0, *fx_exp));
+  }
+}
+
+// Paint particle positions (disp + rsd * mom along rsd_axis) with unit weight.
+template <typename T>
+__global__ void k_paint(Geo g, const T *__restrict__ disp, const T *__restrict__ mom, int rsd_axis,
+                        T rsd, unsigned long long *rho, const int *fx_exp) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.np) return;
+  T d[3] = {disp[p], disp[g.np + p], disp[2 * g.np + p]};
+  if (rsd_axis >= 0) d[rsd_axis] += rsd * mom[rsd_axis * g.np + p];
+  const Cell<T> c = locate<T>(g.L, p, d[0], d[1], d[2]);
+  deposit<T>(g.L, rho, c, (T)ldexp(1.0, *fx_exp));
+}
+
+// One fused leapfrog update: F = readout(Phi, x); p += kick F; x' = x + drift p;
+// paint x' (if rho).  x and x' may alias.
+template <typename T>
+__global__ void k_kdk(Geo g, const V4<T> *__restrict__ phi, const T *x, T *xn, T *__restrict__ mom,
+                      T kick, T drift, unsigned long long *rho, const int *fx_exp) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.np) return;
+  const T x0 = x[p], x1 = x[g.np + p], x2 = x[2 * g.np + p];
+  Cell<T> c = locate<T>(g.L, p, x0, x1, x2);
+  T f0, f1, f2;
+  readout3<T>(g.L, phi, c, f0, f1, f2);
+  const T p0 = mom[p] + kick * f0, p1 = mom[g.np + p] + kick * f1, p2 = mom[2 * g.np + p] + kick * f2;
+  mom[p] = p0;
+  mom[g.np + p] = p1;
+  mom[2 * g.np + p] = p2;
+  const T y0 = x0 + drift * p0, y1 = x1 + drift * p1, y2 = x2 + drift * p2;
+  xn[p] = y0;
+  xn[g.np + p] = y1;
+  xn[2 * g.np + p] = y2;
+  if (rho) {
+    c = locate<T>(g.L, p, y0, y1, y2);
+    deposit<T>(g.L, rho, c, (T)ldexp(1.0, *fx_exp));
+  }
+}
+
+// Last half kick p += kick F(x), then paint x + rsd * p along rsd_axis.
+template <typename T>
+__global__ void k_final(Geo g, const V4<T> *__restrict__ phi, const T *__restrict__ x, T *__restrict__ mom,
+                        T kick, int rsd_axis, T rsd, unsigned long long *rho, const int *fx_exp) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.np) return;
+  T d[3] = {x[p], x[g.np + p], x[2 * g.np + p]};
+  Cell<T> c = locate<T>(g.L, p, d[0], d[1], d[2]);
+  T f[3];
+  readout3<T>(g.L, phi, c, f[0], f[1], f[2]);
+  T m[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    m[a] = mom[a * g.np + p] + kick * f[a];
+    mom[a * g.np + p] = m[a];
+  }
+  if (rho) {
+    if (rsd_axis >= 0) d[rsd_axis] += rsd * m[rsd_axis];
+    c = locate<T>(g.L, p, d[0], d[1], d[2]);
+    deposit<T>(g.L, rho, c, (T)ldexp(1.0, *fx_exp));
+  }
+}
+
+// Plain readout of the force (probe): out = Delta * F at x.
+template <typename T>
+__global__ void k_readout(Geo g, const V4<T> *__restrict__ phi, const T *__restrict__ x, T scale,
+                          T *__restrict__ out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.np) return;
+  const Cell<T> c = locate<T>(g.L, p, x[p], x[g.np + p], x[2 * g.np + p]);
+  T f0, f1, f2;
+  readout3<T>(g.L, phi, c, f0, f1, f2);
+  out[p] = scale * f0;
+  out[g.np + p] = scale * f1;
+  out[2 * g.np + p] = scale * f2;
+}
+
+// Adjoint of the final paint (and RSD): xbar = grad_u sum W(u_s - c) dbar(c);
+// pbar = rsd * xbar along the RSD axis; then the running max of |cn * pbar|.
+template <typename T>
+__global__ void k_adj_final(Geo g, const T *__restrict__ x, const T *__restrict__ mom, int rsd_axis, T rsd,
+                            const T *__restrict__ dbar, T *__restrict__ xbar, T *__restrict__ pbar, T cn,
+                            unsigned long long *maxslot) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T mx = T(0);
+  if (p < g.np) {
+    T d[3] = {x[p], x[g.np + p], x[2 * g.np + p]};
+    if (rsd_axis >= 0) d[rsd_axis] += rsd * mom[rsd_axis * g.np + p];
+    const Cell<T> c = locate<T>(g.L, p, d[0], d[1], d[2]);
+    T gx, gy, gz;
+    grad_gather<T>(g.L, nullptr, dbar, c, T(0), T(0), T(0), gx, gy, gz);
+    T pb[3] = {T(0), T(0), T(0)};
+    const T gg[3] = {gx, gy, gz};
+    if (rsd_axis >= 0) pb[rsd_axis] = rsd * gg[rsd_axis];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xbar[a * g.np + p] = gg[a];
+      pbar[a * g.np + p] = pb[a];
+      mx = max(mx, fabs(cn * pb[a]));
+    }
+  }
+  // warp max then one atomic per warp
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_abs<T>(maxslot, mx);
+}
+
+// 3-channel paint of the force cotangent c_k * pbar at x_k, fixed point with
+// the exponent chosen from the running max.
+template <typename T>
+__global__ void k_adj_paint3(Geo g, const T *__restrict__ x, const T *__restrict__ pbar, T ck,
+                             unsigned long long *m3, const unsigned long long *maxslot, int *fx_exp_out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = fixed_exponent((double)read_max_abs<T>(maxslot), g.log2np);
+  if (p == 0) *fx_exp_out = e;
+  if (p >= g.np) return;
+  const Cell<T> c = locate<T>(g.L, p, x[p], x[g.np + p], x[2 * g.np + p]);
+  const int64_t m = (int64_t)g.np;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T v = ck * pbar[a * g.np + p];
+    if constexpr (sizeof(T) == 4) v = scalbnf(v, e);
+    else v = scalbn(v, e);
+    if (v != T(0)) deposit<T>(g.L, m3 + a * m, c, v);
+  }
+}
+
+// Adjoint gather at x_k: xbar += grad_u sum W (c_k pbar . Phi_k + rhobar);
+// then (if drift != 0) pbar += drift * xbar and the running max of |cnext pbar|.
+template <typename T>
+__global__ void k_adj_gather(Geo g, const T *__restrict__ x, const V4<T> *__restrict__ phi,
+                             const T *__restrict__ rhobar, T ck, T *__restrict__ xbar, T *__restrict__ pbar,
+                             T drift, T cnext, unsigned long long *maxslot) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T mx = T(0);
+  if (p < g.np) {
+    const Cell<T> c = locate<T>(g.L, p, x[p], x[g.np + p], x[2 * g.np + p]);
+    T pb[3] = {pbar[p], pbar[g.np + p], pbar[2 * g.np + p]};
+    T gx, gy, gz;
+    grad_gather<T>(g.L, phi, rhobar, c, ck * pb[0], ck * pb[1], ck * pb[2], gx, gy, gz);
+    const T xb[3] = {xbar[p] + gx, xbar[g.np + p] + gy, xbar[2 * g.np + p] + gz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xbar[a * g.np + p] = xb[a];
+      if (drift != T(0)) {
+        pb[a] += drift * xb[a];
+        pbar[a * g.np + p] = pb[a];
+      }
+      mx = max(mx, fabs(cnext * pb[a]));
+    }
+  }
+  if (maxslot) {
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_abs<T>(maxslot, mx);
+  }
+}
+
+// 2LPT adjoint, per particle (= per Lagrangian node): psi1bar, psi2bar.
+template <typename T>
+__global__ void k_lpt_adj(int64_t np, const T *__restrict__ xbar, const T *__restrict__ pbar, T d1, T d2,
+                          T gp1, T gp2, T inv_cell, T *__restrict__ psi1bar, T *__restrict__ psi2bar) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * np) return;
+  const T xb = xbar[i] * inv_cell, pb = pbar[i] * inv_cell;
+  psi1bar[i] = d1 * xb + gp1 * pb;
+  if (psi2bar) psi2bar[i] = d2 * xb + gp2 * pb;
+}
+
+}  // namespace part
+}  // namespace pm

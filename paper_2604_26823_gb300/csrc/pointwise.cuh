@@ -1,0 +1,198 @@
+// Mesh-wise kernels: IC amplitude table, likelihood + its derivative, the
+// 2LPT source adjoint, deterministic FP64 reductions and small helpers.
+#pragma once
+#include "common.cuh"
+
+namespace pm {
+namespace pw {
+
+constexpr int kRedBlocks = 1024;  // fixed grid of every reduction -> fixed summation order
+constexpr int kRedThreads = 256;
+
+// FP64 block reduction into partial[blockIdx.x] (tree order fixed by threadIdx).
+__device__ __forceinline__ void block_sum_store(double v, double *partial) {
+  __shared__ double sh[kRedThreads];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// out[slot] = sum of partial[0..n) in a fixed order (one block).
+static __global__ void k_sum_partials(const double *__restrict__ partial, int n, double *out) {
+  __shared__ double sh[kRedThreads];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += kRedThreads) acc += partial[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// sum x^2 (prior), block partials
+template <typename T> __global__ void k_sumsq(const T *__restrict__ x, int64_t n, double *partial) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)x[i];
+    acc += v * v;
+  }
+  block_sum_store(acc, partial);
+}
+
+// IC amplitude on the half spectrum: sqrt(P(|k|) / Delta^3), P from the
+// (ln k, ln P) table by linear interpolation, clamped at the ends; A(0) = 0.
+template <typename T>
+__global__ void k_amplitude(T *amp, int n, double kf, double inv_cell3, const double *__restrict__ lnk,
+                            const double *__restrict__ lnp, int npk) {
+  const int h = n / 2 + 1;
+  const int64_t total = (int64_t)n * n * h;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int iz = (int)(i % h);
+  const int iy = (int)((i / h) % n);
+  const int ix = (int)(i / ((int64_t)h * n));
+  const int nx = ix < n / 2 ? ix : ix - n;
+  const int ny = iy < n / 2 ? iy : iy - n;
+  const int n2 = nx * nx + ny * ny + iz * iz;
+  if (n2 == 0) {
+    amp[i] = T(0);
+    return;
+  }
+  const double lk = log(kf * sqrt((double)n2));
+  double lp;
+  if (lk <= lnk[0]) {
+    lp = lnp[0];
+  } else if (lk >= lnk[npk - 1]) {
+    lp = lnp[npk - 1];
+  } else {
+    int lo = 0, hi = npk - 1;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (lnk[mid] <= lk) lo = mid;
+      else hi = mid;
+    }
+    const double slope = (lnp[hi] - lnp[lo]) / (lnk[hi] - lnk[lo]);
+    lp = slope * (lk - lnk[lo]) + lnp[lo];
+  }
+  amp[i] = (T)sqrt(exp(lp) * inv_cell3);
+}
+
+struct LossParams {
+  int lik;           // 0 gaussian, 1 poisson
+  double b, inv_s2;  // gaussian
+  double alpha, delta_th, K, nbar, rho_floor;  // poisson
+  double lw;         // loss weight for the derivative
+};
+
+// Per cell: delta = rho - 1 from the fixed-point density, the likelihood term
+// (block partials in FP64), dbar = lw * d(term)/d delta (+ cot), delta_out.
+template <typename T>
+__global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const int *fx_exp,
+                       const T *__restrict__ data, const T *__restrict__ resp, const T *__restrict__ cot,
+                       T *__restrict__ dbar, T *__restrict__ delta_out, int64_t n, double *partial) {
+  const int e = -__ldg(fx_exp);
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T delta;
+    if constexpr (sizeof(T) == 4) delta = scalbnf(__ll2float_rn(rho[i]), e) - 1.0f;
+    else delta = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
+    if (delta_out) delta_out[i] = delta;
+    const T r = resp[i];
+    T g = T(0);
+    if (lp.lik == 0) {
+      const T res = (T)lp.b * delta - data[i];
+      acc += 0.5 * (double)r * (double)res * (double)res * lp.inv_s2;
+      g = r * (T)lp.b * res * (T)lp.inv_s2;
+    } else if (r > T(0)) {
+      const T onep = T(1) + delta;
+      const T base = onep > (T)lp.rho_floor ? onep : (T)lp.rho_floor;
+      const T sg = T(1) / (T(1) + exp(-(T)lp.K * (delta - (T)lp.delta_th)));
+      const T pw = pow(base, (T)lp.alpha);
+      const T lam = r * (T)lp.nbar * pw * sg;
+      const T cnt = data[i];
+      acc += (double)lam - (double)cnt * (double)log(lam);
+      const T dpow = onep > (T)lp.rho_floor ? (T)lp.alpha * pw / base : T(0);
+      const T dg = dpow * sg + pw * (T)lp.K * sg * (T(1) - sg);
+      g = r * (T)lp.nbar * dg * (T(1) - cnt / lam);
+    }
+    if (dbar) dbar[i] = (T)lp.lw * g + (cot ? cot[i] : T(0));
+  }
+  block_sum_store(acc, partial);
+}
+
+// Model mean per cell from the fixed-point density (mock generation).
+template <typename T>
+__global__ void k_expected(LossParams lp, const long long *__restrict__ rho, const int *fx_exp,
+                           const T *__restrict__ resp, T *__restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int e = -__ldg(fx_exp);
+  T delta;
+  if constexpr (sizeof(T) == 4) delta = scalbnf(__ll2float_rn(rho[i]), e) - 1.0f;
+  else delta = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
+  if (lp.lik == 0) {
+    out[i] = (T)lp.b * delta;
+  } else {
+    const T onep = T(1) + delta;
+    const T base = onep > (T)lp.rho_floor ? onep : (T)lp.rho_floor;
+    const T sg = T(1) / (T(1) + exp(-(T)lp.K * (delta - (T)lp.delta_th)));
+    out[i] = resp[i] > T(0) ? resp[i] * (T)lp.nbar * pow(base, (T)lp.alpha) * sg : T(0);
+  }
+}
+
+// 2LPT source adjoint: S = phi00 phi11 + phi00 phi22 + phi11 phi22
+//                         - phi01^2 - phi02^2 - phi12^2  (slots 0..5 in that order)
+// phibar_ii = Sbar (sum of the other two diagonals), phibar_ij = -2 Sbar phi_ij,
+// written over phi in place.
+template <typename T> __global__ void k_phibar(T *phi, const T *__restrict__ sbar, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T sb = sbar[i];
+  const T p00 = phi[i], p11 = phi[n + i], p22 = phi[2 * n + i];
+  phi[i] = sb * (p11 + p22);
+  phi[n + i] = sb * (p00 + p22);
+  phi[2 * n + i] = sb * (p00 + p11);
+  phi[3 * n + i] = T(-2) * sb * phi[3 * n + i];
+  phi[4 * n + i] = T(-2) * sb * phi[4 * n + i];
+  phi[5 * n + i] = T(-2) * sb * phi[5 * n + i];
+}
+
+// out = a * x (elementwise), used for unit conversions of probe outputs.
+template <typename T> __global__ void k_scale(const T *__restrict__ x, T a, T *__restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i];
+}
+
+// out = y + a * x
+template <typename T>
+__global__ void k_axpy(const T *__restrict__ x, const T *__restrict__ y, double a, T *__restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = y[i] + (T)a * x[i];
+}
+
+// delta = rho - 1 from a fixed-point mesh
+template <typename T>
+__global__ void k_fixed_to_delta(const long long *__restrict__ rho, const int *fx_exp, T *__restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int e = -__ldg(fx_exp);
+  if constexpr (sizeof(T) == 4) out[i] = scalbnf(__ll2float_rn(rho[i]), e) - 1.0f;
+  else out[i] = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
+}
+
+// count of non-finite values (for input validation), block partials
+template <typename T> __global__ void k_count_nonfinite(const T *__restrict__ x, int64_t n, double *partial) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += isfinite(x[i]) ? 0.0 : 1.0;
+  block_sum_store(acc, partial);
+}
+
+}  // namespace pw
+}  // namespace pm

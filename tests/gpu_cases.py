@@ -1,0 +1,83 @@
+"""Shared set-up of the GPU parity tests: configurations mirrored on both
+sides, seeded inputs, and cached oracle results (the oracle runs once per
+configuration per test session)."""
+import functools
+
+import numpy as np
+
+from oracle import cosmology as OC
+from oracle import model as OM
+from paper_2604_26823_gb300 import inputs
+
+
+@functools.lru_cache(maxsize=None)
+def table():
+    return OC.linear_power_table()
+
+
+# name -> (api Config kwargs); the oracle receives the same values
+CASES = {
+    # 32^3 particles in a 128 Mpc/h box, 2LPT to a = 0.1, 5 steps, b = 1.5 Gaussian, full box
+    "small": dict(n=32, box=128.0, n_steps=5, lpt_order=2, rsd_axis=-1, likelihood="gaussian",
+                  bias_b=1.5, sigma=1.0, prior_weight=1.0),
+    # 128^3 in 512 Mpc/h, 10 steps, redshift-space shift along z
+    "rsd128": dict(n=128, box=512.0, n_steps=10, lpt_order=2, rsd_axis=2, likelihood="gaussian",
+                   bias_b=1.5, sigma=1.0, prior_weight=1.0),
+    # masked Poisson likelihood with the power-law + sigmoid bias, 64^3 in 125 Mpc/h
+    "poisson64": dict(n=64, box=125.0, n_steps=4, lpt_order=2, rsd_axis=-1, likelihood="poisson",
+                      nbar_cell=0.5, alpha=0.7, delta_th=1.2, K=3.0, rho_floor=1e-3, prior_weight=1.0),
+    # Zel'dovich start, RSD along x, 16^3 (single-tile meshes)
+    "tiny": dict(n=16, box=48.0, n_steps=3, lpt_order=1, rsd_axis=0, likelihood="gaussian",
+                 bias_b=1.2, sigma=0.8, prior_weight=0.5),
+}
+
+
+def oracle_config(kw):
+    keys = ("n", "box", "n_steps", "lpt_order", "rsd_axis", "likelihood", "bias_b", "sigma", "alpha",
+            "delta_th", "K", "nbar_cell", "rho_floor", "prior_weight")
+    return OM.Config(**{k: kw[k] for k in keys if k in kw})
+
+
+@functools.lru_cache(maxsize=None)
+def case_inputs(name):
+    """(s, data, R) as float64 numpy arrays (exactly representable in float32)."""
+    kw = CASES[name]
+    n = kw["n"]
+    s = inputs.white_noise(n, 2).astype(np.float64)
+    if kw["likelihood"] == "gaussian":
+        data = inputs.normal_field(n, 3).astype(np.float64)
+        resp = np.ones((n, n, n)) if name != "tiny" else inputs.uniform_field(n, 4, 0.0, 1.0).astype(np.float64)
+    else:
+        sel = inputs.survey_selection(n, kw["box"], 4, observer=(62.5, 62.5, -60.0), r_scale=70.0)
+        resp = sel.astype(np.float64)
+        data = inputs.poisson_counts(0.5 * resp * 1.3, 5).astype(np.float64)
+    return s, data, resp
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_gradient(name):
+    cfg = oracle_config(CASES[name])
+    s, data, resp = case_inputs(name)
+    lnk, lnp = table()
+    return OM.gradient(s, cfg, lnk, lnp, data, resp)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_evolve(name):
+    cfg = oracle_config(CASES[name])
+    s, _, _ = case_inputs(name)
+    lnk, lnp = table()
+    disp, mom, _ = OM.evolve(s, cfg, lnk, lnp)
+    return disp, mom
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cosine(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))

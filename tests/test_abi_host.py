@@ -1,0 +1,93 @@
+"""The C-ABI library loads and exports every symbol include/mujica_pm.h
+declares; host-side validation and host coefficients (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import cosmology as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_26823_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "mujica_pm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pm_\w+|lbfgs_\w+|project_rank_match)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "pm_forward" in names and "pm_adjoint" in names and "lbfgs_step" in names
+    assert "project_rank_match" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2604_26823_gb300 import _lib
+    assert set(names) == set(_lib.SIGNATURES), set(names) ^ set(_lib.SIGNATURES)
+
+
+def test_config_struct_layout_matches_header(lib):
+    from paper_2604_26823_gb300 import _lib
+    assert ctypes.sizeof(_lib.pm_config) == 8 * 4 + 11 * 8
+    assert lib.pm_version().decode().startswith("mujica-pm")
+
+
+def test_validation_errors_without_gpu(lib):
+    from paper_2604_26823_gb300 import _lib, api
+    cfg = api.Config(n=48, box=100.0).to_c()
+    nb = ctypes.c_size_t()
+    assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 2   # UNSUPPORTED
+    assert b"power of two" in lib.pm_last_error()
+    cfg = api.Config(n=32, box=-1.0).to_c()
+    assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 1
+    cfg = api.Config(n=32, box=128.0, likelihood="poisson", nbar_cell=0.0).to_c()
+    assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 1
+    cfg = api.Config(n=32, box=128.0).to_c()
+    assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 0
+    assert nb.value > 0
+    # a plan with a too-small workspace is refused before any device call
+    h = ctypes.c_void_p()
+    lnk = np.linspace(-9, 4, 8)
+    lnp = np.zeros(8)
+    st = lib.pm_plan_create(ctypes.byref(cfg), lnk.ctypes.data_as(_lib._DP), lnp.ctypes.data_as(_lib._DP), 8,
+                            ctypes.c_void_p(256), 1024, ctypes.byref(h))
+    assert st == 5
+    st = lib.lbfgs_workspace_bytes(100, 0, 0, ctypes.byref(nb))
+    assert st == 1
+
+
+def test_checkpoint_layout_is_smaller_at_large_step_counts(lib):
+    from paper_2604_26823_gb300 import api
+    nb0, nb2 = ctypes.c_size_t(), ctypes.c_size_t()
+    c0 = api.Config(n=64, box=256.0, n_steps=10).to_c()
+    c2 = api.Config(n=64, box=256.0, n_steps=10, checkpoint_every=2).to_c()
+    assert lib.pm_workspace_bytes(ctypes.byref(c0), ctypes.byref(nb0)) == 0
+    assert lib.pm_workspace_bytes(ctypes.byref(c2), ctypes.byref(nb2)) == 0
+    assert nb2.value < nb0.value
+
+
+def test_host_growth_matches_oracle(lib):
+    from paper_2604_26823_gb300 import api
+    a = np.array([0.1, 0.19, 0.55, 1.0])
+    for om in (0.25, 1.0):
+        got = api.pm_growth(om, a)
+        ref = C.growth(a, om)
+        for k in ("D1", "D2", "Gp1", "Gp2"):
+            np.testing.assert_allclose(got[k], ref[k], rtol=1e-10)
+
+
+def test_host_power_table_matches_oracle(lib):
+    from paper_2604_26823_gb300 import api
+    lnk, lnp = api.pm_linear_power_table()
+    rk, rp = C.linear_power_table()
+    np.testing.assert_allclose(lnk, rk, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(lnp, rp, rtol=0, atol=1e-7)
