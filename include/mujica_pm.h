@@ -201,6 +201,22 @@ pm_status project_rank_match(pm_plan *plan, void *s_inout, uint32_t mode, const 
                              uint64_t rng_seed, uint64_t rng_counter, int64_t *n_reset_out,
                              pm_stream_t stream);
 
+/* Projection step only (z-score, then reset |s_hat| > 10 to the same
+ * counter-based N(0,1) draws as PM_PROJECT) on n elements of the given
+ * precision, in place, WITHOUT any workspace: for callers that cannot give
+ * the library device memory (their GPU memory is owned by another allocator,
+ * or they must not allocate mid-run).  The paper has no counterpart of this
+ * entry point; it repeats the projection of project_rank_match.
+ * Scratch: a file-scope device array of about 512 KB held by every GPU that
+ * loads the library until exit; n must not exceed 2^28 elements
+ * (PM_ERR_UNSUPPORTED otherwise).  The first call on each device looks up the
+ * array's device address (with that device current); make that first call
+ * before any stream capture.  All calls share the array: calls that overlap on
+ * the GPU race and must be serialised.  Allocates nothing; synchronises the
+ * stream.  n_reset_out (nullable host): number of reset values. */
+pm_status pm_project_noalloc(int64_t n, int32_t precision, void *s_inout, uint64_t rng_seed,
+                             uint64_t rng_counter, int64_t *n_reset_out, pm_stream_t stream);
+
 /* ---- L-BFGS (Sec. 2.3.1) ------------------------------------------------ */
 
 pm_status lbfgs_workspace_bytes(int64_t n_elems, int32_t m, int32_t precision, size_t *bytes);

@@ -71,6 +71,7 @@ SIGNATURES = {
     "pm_rom_fourier_counts": (_I32, [_P, _I64P]),
     "pm_count_positive": (_I32, [_P, _P, _I64P, _P]),
     "project_rank_match": (_I32, [_P, _P, _U32, _P, _P, _P, _U64, _U64, _I64P, _P]),
+    "pm_project_noalloc": (_I32, [_I64, _I32, _P, _U64, _U64, _I64P, _P]),
     "lbfgs_workspace_bytes": (_I32, [_I64, _I32, _I32, _SZP]),
     "lbfgs_create": (_I32, [_I64, _I32, _I32, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "lbfgs_destroy": (_I32, [_P]),

@@ -247,6 +247,18 @@ def project_rank_match(plan, s_inout, mode, R=None, targets_real=None, targets_f
     return nres.value
 
 
+def pm_project_noalloc(s_inout, seed=0, counter=0, stream=None):
+    """Projection (z-score + reset) of a CUDA vector in place, with the
+    library's static scratch instead of a workspace.  Returns the number of
+    reset values."""
+    prec = L.PM_PREC_F32 if s_inout.dtype == torch.float32 else L.PM_PREC_F64
+    nres = ctypes.c_int64()
+    L.check(L.load().pm_project_noalloc(s_inout.numel(), prec, _ptr(s_inout, s_inout.dtype, s_inout.numel(), "s"),
+                                        int(seed), int(counter), ctypes.byref(nres), _stream(stream)),
+            "pm_project_noalloc")
+    return nres.value
+
+
 class LBFGS:
     """lbfgs_state plus its device workspace."""
 

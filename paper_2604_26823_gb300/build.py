@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmujica_pm.so")
-SOURCES = ["engine_f32.cu", "engine_f64.cu", "api_model.cu", "lbfgs.cu", "host_cosmo.cpp"]
+SOURCES = ["engine_f32.cu", "engine_f64.cu", "api_model.cu", "lbfgs.cu", "project_static.cu", "host_cosmo.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
