@@ -33,6 +33,7 @@ template <typename T, int N> struct CCfg {
   static constexpr int B = FftCfg<T>::B;
   static constexpr int NT = cmin(N == 512 ? 512 : 256, B * N);
   static constexpr size_t SMEM = (size_t)N * B * sizeof(cx<T>);
+  static constexpr size_t SMEM2 = 2 * SMEM;  // fused x pass: two tiles
 };
 
 #define PM_DISPATCH_N(nval, ...)             \
@@ -335,9 +336,9 @@ template <typename T> struct Engine {
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
       auto kern = fft::k_x_1toM<T, NN, CC::B, CC::NT>;
-      set_smem(kern, CC::SMEM);
+      set_smem(kern, CC::SMEM2);
       ::pm::note_launch();
-      kern<<<(int)(S / n / CC::B), CC::NT, CC::SMEM, st>>>(a, tw);
+      kern<<<(int)(S / n / CC::B), CC::NT, CC::SMEM2, st>>>(a, tw);
     });
     PM_LAUNCH_CHECK();
     return PM_OK;
@@ -356,9 +357,9 @@ template <typename T> struct Engine {
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
       auto kern = fft::k_x_Mto1<T, NN, CC::B, CC::NT>;
-      set_smem(kern, CC::SMEM);
+      set_smem(kern, CC::SMEM2);
       ::pm::note_launch();
-      kern<<<(int)(S / n / CC::B), CC::NT, CC::SMEM, st>>>(a, tw);
+      kern<<<(int)(S / n / CC::B), CC::NT, CC::SMEM2, st>>>(a, tw);
     });
     PM_LAUNCH_CHECK();
     return PM_OK;
@@ -370,9 +371,9 @@ template <typename T> struct Engine {
     PM_DISPATCH_N(n, {
       using Z = ZCfg<T, NN>;
       auto kern = fft::k_z_c2r<T, NN, Z::B, Z::NT, NIN, Out>;
-      set_smem(kern, Z::SMEM);
+      set_smem(kern, NIN * Z::SMEM);
       ::pm::note_launch();
-      kern<<<(int)((int64_t)nb * n * n / Z::B), Z::NT, Z::SMEM, st>>>(ins, out, tw);
+      kern<<<(int)((int64_t)nb * n * n / Z::B), Z::NT, NIN * Z::SMEM, st>>>(ins, out, tw);
     });
     PM_LAUNCH_CHECK();
     return PM_OK;

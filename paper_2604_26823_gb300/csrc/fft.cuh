@@ -314,76 +314,65 @@ struct XArgsN {  // up to 9 input spectra -> one output spectrum
 };
 
 // x pass, case "one to many": X = FFT_x(in); out_o = IFFT_x(h_o X), o < count.
+// Shared memory holds the transformed input (kept) and one work tile.
 template <typename T, int N, int B, int NT>
 __global__ void __launch_bounds__(NT) k_x_1toM(XArgs1 a, const cx<T> *__restrict__ tw) {
   using C = cx<T>;
   constexpr int H = N / 2 + 1;
-  constexpr int PE = N * B / NT;
   static_assert(N * B % NT == 0, "tile must split evenly over threads");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *buf = reinterpret_cast<C *>(smem_raw);
+  C *xin = reinterpret_cast<C *>(smem_raw);
+  C *buf = xin + N * B;
   const int col0 = blockIdx.x * B;
   const int64_t astride = (int64_t)N * H;
   const C *src = reinterpret_cast<const C *>(a.in) + col0;
-  for (int e = threadIdx.x; e < N * B; e += NT) buf[e] = src[(e / B) * astride + e % B];
+  for (int e = threadIdx.x; e < N * B; e += NT) xin[e] = src[(e / B) * astride + e % B];
   __syncthreads();
-  smem_fft<C, N, B, B, NT, -1>(buf, tw, 1);
-  C x[PE];
-#pragma unroll
-  for (int q = 0; q < PE; ++q) x[q] = buf[threadIdx.x + q * NT];
+  smem_fft<C, N, B, B, NT, -1>(xin, tw, 1);
   for (int o = 0; o < a.mult.count; ++o) {
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PE; ++q) {
-      const int e = threadIdx.x + q * NT;
+    for (int e = threadIdx.x; e < N * B; e += NT) {
       int64_t flat;
       const ModeK<T> mk = xpass_mode<T>(e, B, col0, N, (T)a.kf, flat);
       const T amp = (a.mult.m[o].flags & M_AMP) ? reinterpret_cast<const T *>(a.amp)[flat] : T(0);
-      buf[e] = apply_mult<T, C>(a.mult.m[o], x[q], mk, amp);
+      buf[e] = apply_mult<T, C>(a.mult.m[o], xin[e], mk, amp);
     }
     __syncthreads();
     smem_fft<C, N, B, B, NT, +1>(buf, tw, 1);
     C *dst = reinterpret_cast<C *>(a.out[o]) + col0;
     for (int e = threadIdx.x; e < N * B; e += NT) dst[(e / B) * astride + e % B] = buf[e];
+    __syncthreads();
   }
 }
 
 // x pass, case "many to one": out = IFFT_x( sum_i h_i FFT_x(in_i) ).
+// Shared memory holds one work tile and the accumulator.
 template <typename T, int N, int B, int NT>
 __global__ void __launch_bounds__(NT) k_x_Mto1(XArgsN a, const cx<T> *__restrict__ tw) {
   using C = cx<T>;
   constexpr int H = N / 2 + 1;
-  constexpr int PE = N * B / NT;
   static_assert(N * B % NT == 0, "tile must split evenly over threads");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
+  C *acc = buf + N * B;
   const int col0 = blockIdx.x * B;
   const int64_t astride = (int64_t)N * H;
-  C acc[PE];
-#pragma unroll
-  for (int q = 0; q < PE; ++q) acc[q] = mkc<C>(T(0), T(0));
   for (int i = 0; i < a.mult.count; ++i) {
     const C *src = reinterpret_cast<const C *>(a.in[i]) + col0;
-    __syncthreads();
     for (int e = threadIdx.x; e < N * B; e += NT) buf[e] = src[(e / B) * astride + e % B];
     __syncthreads();
     smem_fft<C, N, B, B, NT, -1>(buf, tw, 1);
-#pragma unroll
-    for (int q = 0; q < PE; ++q) {
-      const int e = threadIdx.x + q * NT;
+    for (int e = threadIdx.x; e < N * B; e += NT) {
       int64_t flat;
       const ModeK<T> mk = xpass_mode<T>(e, B, col0, N, (T)a.kf, flat);
       const T amp = (a.mult.m[i].flags & M_AMP) ? reinterpret_cast<const T *>(a.amp)[flat] : T(0);
-      acc[q] = cadd(acc[q], apply_mult<T, C>(a.mult.m[i], buf[e], mk, amp));
+      const C h = apply_mult<T, C>(a.mult.m[i], buf[e], mk, amp);
+      acc[e] = i ? cadd(acc[e], h) : h;
     }
+    __syncthreads();
   }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < PE; ++q) buf[threadIdx.x + q * NT] = acc[q];
-  __syncthreads();
-  smem_fft<C, N, B, B, NT, +1>(buf, tw, 1);
+  smem_fft<C, N, B, B, NT, +1>(acc, tw, 1);
   C *dst = reinterpret_cast<C *>(a.out) + col0;
-  for (int e = threadIdx.x; e < N * B; e += NT) dst[(e / B) * astride + e % B] = buf[e];
+  for (int e = threadIdx.x; e < N * B; e += NT) dst[(e / B) * astride + e % B] = acc[e];
 }
 
 struct Ins {
@@ -392,21 +381,20 @@ struct Ins {
 
 // z pass, half complex -> real (unnormalised) for NIN spectra sharing rows;
 // Out::put(row, m, v[NIN]) receives the real pair (x_{2m}, x_{2m+1}) of each.
+// Each input is transformed in its own shared-memory tile.
 template <typename T, int N, int B, int NT, int NIN, class Out>
 __global__ void __launch_bounds__(NT) k_z_c2r(Ins ins, Out out, const cx<T> *__restrict__ tw) {
   using C = cx<T>;
   constexpr int LEN = N / 2;
   constexpr int SB = B + 1;
-  constexpr int PE = B * LEN / NT;
   static_assert(B * LEN % NT == 0, "tile must split evenly over threads");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *buf = reinterpret_cast<C *>(smem_raw);
+  C *bufs = reinterpret_cast<C *>(smem_raw);
   const int64_t row0 = (int64_t)blockIdx.x * B;
-  C v[NIN][PE];
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < NIN; ++i) {
+    C *buf = bufs + i * LEN * SB;
     const C *src = reinterpret_cast<const C *>(ins.p[i]);
-    if (i) __syncthreads();
     for (int e = threadIdx.x; e < B * LEN; e += NT) {
       const int row = e / LEN, k = e % LEN;
       const C *rp = src + (row0 + row) * (LEN + 1);
@@ -422,18 +410,12 @@ __global__ void __launch_bounds__(NT) k_z_c2r(Ins ins, Out out, const cx<T> *__r
     }
     __syncthreads();
     smem_fft<C, LEN, B, SB, NT, +1>(buf, tw, 2);
-#pragma unroll
-    for (int q = 0; q < PE; ++q) {
-      const int e = threadIdx.x + q * NT;
-      v[i][q] = buf[(e % LEN) * SB + e / LEN];
-    }
   }
-#pragma unroll
-  for (int q = 0; q < PE; ++q) {
-    const int e = threadIdx.x + q * NT;
+#pragma unroll 2
+  for (int e = threadIdx.x; e < B * LEN; e += NT) {
     C w[NIN];
 #pragma unroll
-    for (int i = 0; i < NIN; ++i) w[i] = v[i][q];
+    for (int i = 0; i < NIN; ++i) w[i] = bufs[i * LEN * SB + (e % LEN) * SB + e / LEN];
     out.put(row0 + e / LEN, e % LEN, w);
   }
 }

@@ -63,6 +63,26 @@ def oracle_gradient(name):
 
 
 @functools.lru_cache(maxsize=None)
+def oracle_gradient_single_fft(name):
+    """The oracle's gradient with every FFT step evaluated in single precision
+    (scipy.fft on float32 data): an independent FP32 evaluation of the same
+    algorithm, used to bound what any FP32 trajectory can reach."""
+    import scipy.fft as sf
+    from oracle import mesh as OMesh
+    r64, i64 = OMesh.rfft3, OMesh.irfft3
+    OMesh.rfft3 = lambda f: sf.rfftn(np.asarray(f, np.float32)).astype(np.complex128)
+    OMesh.irfft3 = lambda fk, n: sf.irfftn(np.asarray(fk, np.complex64), s=(n, n, n),
+                                           axes=(0, 1, 2)).astype(np.float64)
+    try:
+        cfg = oracle_config(CASES[name])
+        s, data, resp = case_inputs(name)
+        lnk, lnp = table()
+        return OM.gradient(s, cfg, lnk, lnp, data, resp)
+    finally:
+        OMesh.rfft3, OMesh.irfft3 = r64, i64
+
+
+@functools.lru_cache(maxsize=None)
 def oracle_evolve(name):
     cfg = oracle_config(CASES[name])
     s, _, _ = case_inputs(name)

@@ -1,0 +1,87 @@
+"""The benchmark configuration at full size (256^3, 10 steps, masked Poisson
+likelihood, the launch configuration bench.py times), checked through
+properties that hold at any size -- the FP64 oracle cannot evaluate a 256^3
+gradient in test time:
+  * FP32 path vs the all-FP64 GPU path: loss and density within 1e-5, the
+    gradient's cosine >= 0.99999;
+  * the FP64 path's gradient against its own central differences along
+    seeded random directions (eps = 1e-3);
+  * bit-identical repeated evaluation, and bit-identical gradients with
+    particle-state checkpointing every 2 steps.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N = 256
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import bench
+    from paper_2604_26823_gb300 import api, build, inputs
+    build.build()
+    lnk, lnp = api.pm_linear_power_table()
+    R, s_true, nbar_cell = bench.mock_inputs(api, inputs, bench.config(api, 1.0), lnk, lnp, 0)
+    plan32 = api.Plan(bench.config(api, nbar_cell, "f32"), lnk, lnp)
+    dev32 = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+    lam = api.pm_expected_counts(plan32, dev32(s_true), dev32(R))
+    counts = inputs.poisson_counts(lam.cpu().numpy(), 3)
+    s0 = inputs.white_noise(N, 2)
+    return dict(api=api, bench=bench, lnk=lnk, lnp=lnp, R=R, counts=counts, s0=s0, nbar=nbar_cell,
+                plan32=plan32)
+
+
+def _eval(api, plan, s, counts, R, dtype):
+    d = lambda x: torch.tensor(x, dtype=dtype, device="cuda")
+    delta = torch.empty((N, N, N), dtype=dtype, device="cuda")
+    loss = api.pm_forward(plan, d(s), d(counts), d(R), delta_out=delta)
+    l2, g = api.pm_adjoint(plan, d(s), d(counts), d(R))
+    assert l2 == loss
+    return loss, delta.double().cpu().numpy(), g.double().cpu().numpy()
+
+
+def test_fp32_vs_fp64_at_full_size(setup):
+    api, bench = setup["api"], setup["bench"]
+    l32, d32, g32 = _eval(api, setup["plan32"], setup["s0"], setup["counts"], setup["R"], torch.float32)
+    plan64 = api.Plan(bench.config(api, setup["nbar"], "f64"), setup["lnk"], setup["lnp"])
+    l64, d64, g64 = _eval(api, plan64, setup["s0"], setup["counts"], setup["R"], torch.float64)
+    del plan64
+    assert abs(l32 - l64) < 1e-5 * abs(l64)
+    assert np.linalg.norm(d32 - d64) / np.linalg.norm(d64) < 1e-5
+    cos = float(g32.ravel() @ g64.ravel() / (np.linalg.norm(g32) * np.linalg.norm(g64)))
+    assert cos > 0.99999
+    assert np.linalg.norm(g32 - g64) / np.linalg.norm(g64) < 2e-3
+
+
+def test_fp64_gradient_against_finite_differences(setup):
+    api, bench = setup["api"], setup["bench"]
+    from paper_2604_26823_gb300 import inputs
+    plan64 = api.Plan(bench.config(api, setup["nbar"], "f64"), setup["lnk"], setup["lnp"])
+    d = lambda x: torch.tensor(x, dtype=torch.float64, device="cuda")
+    s, c, R = d(setup["s0"]), d(setup["counts"]), d(setup["R"])
+    _, g = api.pm_adjoint(plan64, s, c, R)
+    errs = []
+    for u in inputs.random_unit_directions(N, 4, 100):
+        u = d(u)
+        fd = (api.pm_forward(plan64, s + 1e-3 * u, c, R) - api.pm_forward(plan64, s - 1e-3 * u, c, R)) / 2e-3
+        gu = float((g * u).sum())
+        errs.append(abs(fd - gu) / (abs(gu) + 1e-3 * float(g.norm())))
+    del plan64
+    assert max(errs) < 1e-3, errs
+
+
+def test_repeatable_and_checkpoint_identical(setup):
+    api, bench = setup["api"], setup["bench"]
+    d = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+    s, c, R = d(setup["s0"]), d(setup["counts"]), d(setup["R"])
+    la, ga = api.pm_adjoint(setup["plan32"], s, c, R)
+    lb, gb = api.pm_adjoint(setup["plan32"], s, c, R)
+    assert la == lb and torch.equal(ga, gb)
+    cfg = bench.config(api, setup["nbar"], "f32")
+    cfg.checkpoint_every = 2
+    plan_ck = api.Plan(cfg, setup["lnk"], setup["lnp"])
+    lc, gc = api.pm_adjoint(plan_ck, s, c, R)
+    assert lc == la and torch.equal(gc, ga)
