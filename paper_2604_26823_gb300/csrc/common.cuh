@@ -44,6 +44,80 @@ __device__ __forceinline__ void fx_add(unsigned long long *p, long long q) {
   atomicAdd(p, (unsigned long long)q);
 }
 
+// FP32 <-> int64 conversions written with integer operations from the
+// IEEE-754 binary32 layout (round to nearest, ties to even).  The hardware
+// conversions between FP32 and 64-bit integers issue on the FP64 unit,
+// which is narrow on this GPU and limited the fixed-point paint; these use
+// the integer and bit-manipulation units instead.  Both are host-callable
+// so they can be checked exhaustively on the CPU.
+__host__ __device__ __forceinline__ unsigned fx_f32_bits(float w) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(w);
+#else
+  unsigned b;
+  __builtin_memcpy(&b, &w, 4);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float fx_bits_f32(unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float w;
+  __builtin_memcpy(&w, &b, 4);
+  return w;
+#endif
+}
+__host__ __device__ __forceinline__ int fx_clz64(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return __builtin_clzll(v);
+#endif
+}
+
+// rint(w) as int64 for |w| < 2^62 (larger magnitudes saturate the shift).
+__host__ __device__ __forceinline__ long long fx_f32_to_i64(float w) {
+  const unsigned b = fx_f32_bits(w);
+  const int be = (int)((b >> 23) & 0xffu);
+  if (be < 126) return 0;  // |w| < 0.5, zero and subnormals
+  const unsigned m = (b & 0x7fffffu) | 0x800000u;  // |w| = m * 2^(be - 150)
+  const int sh = be - 150;
+  unsigned long long mag;
+  if (sh >= 0) {
+    mag = (unsigned long long)m << (sh < 39 ? sh : 39);
+  } else {
+    const int r = -sh;  // 1 .. 24
+    unsigned q = m >> r;
+    const unsigned rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
+    q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
+    mag = q;
+  }
+  return (b >> 31) ? -(long long)mag : (long long)mag;
+}
+
+// Nearest float to the int64 q.
+__host__ __device__ __forceinline__ float fx_i64_to_f32(long long q) {
+  if (q == 0) return 0.0f;
+  const unsigned long long mag = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+  int ex = 63 - fx_clz64(mag);  // position of the leading bit
+  unsigned long long mm;
+  if (ex <= 23) {
+    mm = mag << (23 - ex);
+  } else {
+    const int sh = ex - 23;  // 1 .. 40
+    mm = mag >> sh;
+    const unsigned long long rem = mag & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    mm += (rem > half || (rem == half && (mm & 1ull))) ? 1ull : 0ull;
+    if (mm >> 24) {  // rounding carried into a new leading bit
+      mm >>= 1;
+      ++ex;
+    }
+  }
+  const unsigned bits = ((unsigned)(ex + 127) << 23) | ((unsigned)mm & 0x7fffffu);
+  return fx_bits_f32(bits | (q < 0 ? 0x80000000u : 0u));
+}
+
 // ---- launch geometry ----------------------------------------------------
 constexpr int kSMs = 152;
 

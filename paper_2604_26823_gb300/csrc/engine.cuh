@@ -411,6 +411,14 @@ template <typename T> struct Engine {
     PM_CUDA_TRY(cudaMemsetAsync(fx, 0, (size_t)channels * M * sizeof(long long), st));
     return PM_OK;
   }
+  // One deposition launch of a particle source into the fixed-point
+  // channels of fx (Src::NCH planes of M cells).
+  template <class Src> pm_status deposit(Src s) {
+    ::pm::note_launch();
+    part::k_deposit<T, Src><<<grid_for(M, 256), 256, 0, st>>>(geo(), s, reinterpret_cast<unsigned long long *>(fx), M);
+    PM_LAUNCH_CHECK();
+    return PM_OK;
+  }
 
   // ---- forward stages ----
   // 2LPT: fills disp0 / mom (cell units), phi_ij (when keep), paints density.
@@ -453,13 +461,9 @@ template <typename T> struct Engine {
       PM_TRY(set_exp(0, rho_exp));
     }
     const double ic = 1.0 / cell;
-    ::pm::note_launch();
-    part::k_lpt_init<T><<<grid_for(M, 256), 256, 0, st>>>(geo(), psi, psi2, (T)(d1 * ic), (T)(d2 * ic),
-                                                           (T)(gp1 * ic), (T)(gp2 * ic), disp0, mom,
-                                                           paint ? reinterpret_cast<unsigned long long *>(fx) : nullptr,
-                                                           fx_exp, cfg.lpt_order == 2);
-    PM_LAUNCH_CHECK();
-    return PM_OK;
+    const part::Geo g = geo();
+    return deposit(part::SrcLpt<T>{g.L, M, psi, cfg.lpt_order == 2 ? psi2 : nullptr, (T)(d1 * ic), (T)(d2 * ic),
+                                       (T)(gp1 * ic), (T)(gp2 * ic), disp0, mom, paint ? fx_exp : nullptr, T(0)});
   }
 
   // PM force mesh (cell units) from the painted density in fx channel 0.
@@ -490,11 +494,9 @@ template <typename T> struct Engine {
       PM_TRY(memset_fx(1));
       {
         ProfScope ps(prof, P_KDK, st, (double)M * (16 * sizeof(T) + 8));
-        ::pm::note_launch();
-        part::k_kdk<T><<<grid_for(M, 256), 256, 0, st>>>(g, pstate(si), dstate(si), dstate(so), momb, (T)ck[k],
-                                                         (T)dr[k], reinterpret_cast<unsigned long long *>(fx), fx_exp);
+        PM_TRY(deposit(part::SrcKdk<T>{g.L, M, pstate(si), dstate(si), dstate(so), momb, (T)ck[k], (T)dr[k],
+                                           fx_exp, T(0)}));
       }
-      PM_LAUNCH_CHECK();
       PM_TRY(force_mesh(pstate(so)));
     }
     return PM_OK;
@@ -530,12 +532,8 @@ template <typename T> struct Engine {
     }
     const int fin = (keep && keep_all()) ? ns : 0;
     PM_TRY(memset_fx(1));
-    ::pm::note_launch();
-    part::k_final<T><<<grid_for(M, 256), 256, 0, st>>>(geo(), pstate(fin), dstate(fin), mom, (T)ck[ns],
-                                                       cfg.rsd_axis, (T)rsd,
-                                                       reinterpret_cast<unsigned long long *>(fx), fx_exp);
-    PM_LAUNCH_CHECK();
-    return PM_OK;
+    return deposit(part::SrcFinal<T>{geo().L, M, pstate(fin), dstate(fin), mom, (T)ck[ns], cfg.rsd_axis, (T)rsd,
+                                         fx_exp, T(0)});
   }
 
   pm_status loss_terms(const T *s, const T *data, const T *R, const T *cot, double lw, bool want_dbar,
@@ -611,11 +609,8 @@ template <typename T> struct Engine {
     PM_TRY(memset_fx(3));
     {
       ProfScope ps(prof, P_ADJ_PAINT, st, (double)M * (6 * sizeof(T) + 24));
-      ::pm::note_launch();
-      part::k_adj_paint3<T><<<nb, 256, 0, st>>>(g, xk, pbar, (T)ck[k], reinterpret_cast<unsigned long long *>(fx),
-                                                 maxslot, fx_exp + 1);
+      PM_TRY(deposit(part::SrcAdj3<T>{g.L, M, g.log2np, xk, pbar, (T)ck[k], maxslot, fx_exp + 1, 0}));
     }
-    PM_LAUNCH_CHECK();
     PM_TRY(adjoint_force(src));
     PM_CUDA_TRY(cudaMemsetAsync(maxslot, 0, sizeof(unsigned long long), st));
     const T drift = k > 0 ? (T)dr[k - 1] : T(0);
@@ -656,10 +651,7 @@ template <typename T> struct Engine {
                                     cudaMemcpyDeviceToDevice, st));
         PM_TRY(memset_fx(1));
         PM_TRY(set_exp(0, rho_exp));
-        ::pm::note_launch();
-        part::k_paint<T><<<nb, 256, 0, st>>>(g, dstate(0), psi2, -1, T(0),
-                                             reinterpret_cast<unsigned long long *>(fx), fx_exp);
-        PM_LAUNCH_CHECK();
+        PM_TRY(deposit(part::SrcPaint<T>{g.L, M, dstate(0), psi2, -1, T(0), fx_exp, T(0)}));
         PM_TRY(force_mesh(pstate(0)));
         PM_TRY(run_steps(lo, hi, lo, true, psi2));
         for (int k = hi; k >= lo; --k) PM_TRY(reverse_step(k, dstate(k - lo), pstate(k - lo)));
@@ -759,10 +751,7 @@ template <typename T> struct Engine {
     PM_LAUNCH_CHECK();
     PM_TRY(memset_fx(1));
     PM_TRY(set_exp(0, rho_exp));
-    ::pm::note_launch();
-    part::k_paint<T><<<grid_for(M, 256), 256, 0, st>>>(geo(), dstate(0), mom, -1, T(0),
-                                                       reinterpret_cast<unsigned long long *>(fx), fx_exp);
-    PM_LAUNCH_CHECK();
+    PM_TRY(deposit(part::SrcPaint<T>{geo().L, M, dstate(0), mom, -1, T(0), fx_exp, T(0)}));
     if (density_out) {
       ::pm::note_launch();
       pw::k_fixed_to_delta<T><<<grid_for(M, 256), 256, 0, st>>>(fx, fx_exp, density_out, M);
@@ -778,10 +767,8 @@ template <typename T> struct Engine {
     PM_TRY(lpt(s, dstate(0), true));
     PM_TRY(force_mesh(pstate(0)));
     PM_TRY(run_steps(0, cfg.n_steps, 0, false, mom));
-    ::pm::note_launch();
-    part::k_final<T><<<grid_for(M, 256), 256, 0, st>>>(geo(), pstate(0), dstate(0), mom, (T)ck[cfg.n_steps], -1,
-                                                       T(0), nullptr, fx_exp);
-    PM_LAUNCH_CHECK();
+    PM_TRY(deposit(part::SrcFinal<T>{geo().L, M, pstate(0), dstate(0), mom, (T)ck[cfg.n_steps], -1, T(0),
+                                         nullptr, T(0)}));
     const int nb = grid_for(3 * M, 256);
     ::pm::note_launch();
     pw::k_scale<T><<<nb, 256, 0, st>>>(dstate(0), (T)cell, disp_out, 3 * M);

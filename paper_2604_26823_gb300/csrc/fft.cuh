@@ -204,6 +204,18 @@ __device__ __forceinline__ C apply_mult(const MultDesc &d, C x, const ModeK<T> &
 
 // ---- kernels ------------------------------------------------------------
 
+// Tile gather into shared memory: every thread issues all PER of its loads
+// before its first shared store, so PER independent loads per thread are in
+// flight (the passes are bound by HBM latency, not by arithmetic).
+template <int PER, int NT, typename V, class Ld, class St>
+__device__ __forceinline__ void gather_tile(Ld ld, St st) {
+  V r[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) r[q] = ld(threadIdx.x + q * NT);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) st(threadIdx.x + q * NT, r[q]);
+}
+
 // Input loaders of the real z pass: a real mesh of type T, or a fixed-point
 // (int64, value * 2^E) mesh converted on the fly.
 template <typename T> struct LoadReal {
@@ -221,8 +233,8 @@ template <typename T> struct LoadFixed {
     const longlong2 v = reinterpret_cast<const longlong2 *>(p)[i];
     const int e = -__ldg(exp);
     if constexpr (sizeof(T) == 4) {
-      a = scalbnf(__ll2float_rn(v.x), e);
-      b = scalbnf(__ll2float_rn(v.y), e);
+      a = scalbnf(fx_i64_to_f32(v.x), e);
+      b = scalbnf(fx_i64_to_f32(v.y), e);
     } else {
       a = scalbn(__ll2double_rn(v.x), e);
       b = scalbn(__ll2double_rn(v.y), e);
@@ -240,13 +252,15 @@ __global__ void __launch_bounds__(NT) k_z_r2c(Load in, cx<T> *__restrict__ out,
   constexpr int SB = B + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
+  static_assert(B * LEN % NT == 0, "tile must split evenly over threads");
   const int64_t row0 = (int64_t)blockIdx.x * B;
-  for (int e = threadIdx.x; e < B * LEN; e += NT) {
-    const int row = e / LEN, m = e % LEN;
-    T a, b;
-    in.pair((row0 + row) * LEN + m, a, b);
-    buf[m * SB + row] = mkc<C>(a, b);
-  }
+  gather_tile<B * LEN / NT, NT, C>(
+      [&](int e) {
+        T a, b;
+        in.pair(row0 * LEN + e, a, b);
+        return mkc<C>(a, b);
+      },
+      [&](int e, C v) { buf[(e % LEN) * SB + e / LEN] = v; });
   __syncthreads();
   smem_fft<C, LEN, B, SB, NT, -1>(buf, tw, 2);
   for (int e = threadIdx.x; e < B * (LEN + 1); e += NT) {
@@ -274,10 +288,13 @@ __global__ void __launch_bounds__(NT) k_col(const cx<T> *in, cx<T> *out, int64_t
   const int ncol = min(B, ncols - col0);
   const C *src = in + b * bstride + col0;
   C *dst = out + b * bstride + col0;
-  for (int e = threadIdx.x; e < LEN * B; e += NT) {
-    const int pos = e / B, c = e % B;
-    buf[e] = (c < ncol) ? src[pos * astride + c] : mkc<C>(T(0), T(0));
-  }
+  static_assert(LEN * B % NT == 0, "tile must split evenly over threads");
+  gather_tile<LEN * B / NT, NT, C>(
+      [&](int e) {
+        const int pos = e / B, c = e % B;
+        return (c < ncol) ? src[pos * astride + c] : mkc<C>(T(0), T(0));
+      },
+      [&](int e, C v) { buf[e] = v; });
   __syncthreads();
   smem_fft<C, LEN, B, B, NT, SIGN>(buf, tw, 1);
   for (int e = threadIdx.x; e < LEN * B; e += NT) {
@@ -326,7 +343,8 @@ __global__ void __launch_bounds__(NT) k_x_1toM(XArgs1 a, const cx<T> *__restrict
   const int col0 = blockIdx.x * B;
   const int64_t astride = (int64_t)N * H;
   const C *src = reinterpret_cast<const C *>(a.in) + col0;
-  for (int e = threadIdx.x; e < N * B; e += NT) xin[e] = src[(e / B) * astride + e % B];
+  gather_tile<N * B / NT, NT, C>([&](int e) { return src[(e / B) * astride + e % B]; },
+                                 [&](int e, C v) { xin[e] = v; });
   __syncthreads();
   smem_fft<C, N, B, B, NT, -1>(xin, tw, 1);
   for (int o = 0; o < a.mult.count; ++o) {
@@ -358,7 +376,8 @@ __global__ void __launch_bounds__(NT) k_x_Mto1(XArgsN a, const cx<T> *__restrict
   const int64_t astride = (int64_t)N * H;
   for (int i = 0; i < a.mult.count; ++i) {
     const C *src = reinterpret_cast<const C *>(a.in[i]) + col0;
-    for (int e = threadIdx.x; e < N * B; e += NT) buf[e] = src[(e / B) * astride + e % B];
+    gather_tile<N * B / NT, NT, C>([&](int e) { return src[(e / B) * astride + e % B]; },
+                                   [&](int e, C v) { buf[e] = v; });
     __syncthreads();
     smem_fft<C, N, B, B, NT, -1>(buf, tw, 1);
     for (int e = threadIdx.x; e < N * B; e += NT) {
@@ -395,19 +414,26 @@ __global__ void __launch_bounds__(NT) k_z_c2r(Ins ins, Out out, const cx<T> *__r
   for (int i = 0; i < NIN; ++i) {
     C *buf = bufs + i * LEN * SB;
     const C *src = reinterpret_cast<const C *>(ins.p[i]);
-    for (int e = threadIdx.x; e < B * LEN; e += NT) {
-      const int row = e / LEN, k = e % LEN;
-      const C *rp = src + (row0 + row) * (LEN + 1);
-      C xk = rp[k];
-      C xc = cconj(rp[LEN - k]);
-      if (k == 0) {
-        xk.y = T(0);
-        xc.y = T(0);
-      }
-      const C ev = cadd(xk, xc);
-      const C od = cmul(csub(xk, xc), cconj(__ldg(&tw[k])));
-      buf[k * SB + row] = mkc<C>(ev.x - od.y, ev.y + od.x);  // ev + i od
-    }
+    struct Pair {
+      C k, c;
+    };
+    gather_tile<B * LEN / NT, NT, Pair>(
+        [&](int e) {
+          const C *rp = src + (row0 + e / LEN) * (LEN + 1);
+          const int k = e % LEN;
+          return Pair{rp[k], rp[LEN - k]};
+        },
+        [&](int e, Pair pr) {
+          const int row = e / LEN, k = e % LEN;
+          C xk = pr.k, xc = cconj(pr.c);
+          if (k == 0) {
+            xk.y = T(0);
+            xc.y = T(0);
+          }
+          const C ev = cadd(xk, xc);
+          const C od = cmul(csub(xk, xc), cconj(__ldg(&tw[k])));
+          buf[k * SB + row] = mkc<C>(ev.x - od.y, ev.y + od.x);  // ev + i od
+        });
     __syncthreads();
     smem_fft<C, LEN, B, SB, NT, +1>(buf, tw, 2);
   }

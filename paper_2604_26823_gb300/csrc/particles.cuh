@@ -49,14 +49,14 @@ __device__ __forceinline__ int64_t mesh_index(const Lattice &L, int x, int y, in
   return ((((int64_t)x) << L.logn | y) << L.logn) | z;
 }
 
-// Deposit weight v (already scaled by 2^E) onto the 8 nodes, integer atomics.
-template <typename T>
-__device__ __forceinline__ void deposit(const Lattice &L, unsigned long long *mesh, const Cell<T> &c, T v) {
-  const int x1 = (c.c[0] + 1) & L.mask, y1 = (c.c[1] + 1) & L.mask, z1 = (c.c[2] + 1) & L.mask;
+// The 8 CIC deposits of weight v (already scaled by 2^E) as integers
+// q = rint(w * v), handed to f(ox, oy, oz, q) for every non-zero q.  Every
+// deposit path rounds through this one expression, so they agree bit for bit.
+template <typename T, class F>
+__device__ __forceinline__ void cic_corners(const Cell<T> &c, T v, F &&f) {
   const T wx[2] = {T(1) - c.f[0], c.f[0]};
   const T wy[2] = {T(1) - c.f[1], c.f[1]};
   const T wz[2] = {T(1) - c.f[2], c.f[2]};
-  const int xs[2] = {c.c[0], x1}, ys[2] = {c.c[1], y1}, zs[2] = {c.c[2], z1};
 #pragma unroll
   for (int ox = 0; ox < 2; ++ox)
 #pragma unroll
@@ -66,11 +66,19 @@ __device__ __forceinline__ void deposit(const Lattice &L, unsigned long long *me
       for (int oz = 0; oz < 2; ++oz) {
         const T w = wxy * wz[oz];
         long long q;
-        if constexpr (sizeof(T) == 4) q = __float2ll_rn(w);
+        if constexpr (sizeof(T) == 4) q = fx_f32_to_i64(w);
         else q = __double2ll_rn(w);
-        if (q) fx_add(mesh + mesh_index(L, xs[ox], ys[oy], zs[oz]), q);
+        if (q) f(ox, oy, oz, q);
       }
     }
+}
+
+// Deposit onto the 8 nodes with global integer atomics.
+template <typename T>
+__device__ __forceinline__ void deposit(const Lattice &L, unsigned long long *mesh, const Cell<T> &c, T v) {
+  cic_corners<T>(c, v, [&](int ox, int oy, int oz, long long q) {
+    fx_add(mesh + mesh_index(L, (c.c[0] + ox) & L.mask, (c.c[1] + oy) & L.mask, (c.c[2] + oz) & L.mask), q);
+  });
 }
 
 // F = sum_c W(u - c) Phi(c) over a 4-component mesh (x, y, z used).
@@ -161,87 +169,173 @@ struct Geo {
   int log2np;
 };
 
-// disp = (D1 psi1 + D2 psi2)/Delta, mom = (Gp1 psi1 + Gp2 psi2)/Delta (cell units),
-// then paint disp into the fixed-point density.
-template <typename T>
-__global__ void k_lpt_init(Geo g, const T *__restrict__ psi1, const T *__restrict__ psi2, T d1, T d2,
-                           T gp1, T gp2, T *__restrict__ disp, T *__restrict__ mom,
-                           unsigned long long *rho, const int *fx_exp, int use_psi2) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= g.np) return;
-  T d[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const T a1 = psi1[a * g.np + p];
-    const T a2 = use_psi2 ? psi2[a * g.np + p] : T(0);
-    d[a] = d1 * a1 + d2 * a2;
-    disp[a * g.np + p] = d[a];
-    mom[a * g.np + p] = gp1 * a1 + gp2 * a2;
-  }
-  if (rho) {
-    const Cell<T> c = locate<T>(g.L, p, d[0], d[1], d[2]);
-    deposit<T>(g.L, rho, c, (T)ldexp(1.0, *fx_exp));
-  }
-}
+// ---- particle sources of the deposition kernel ---------------------------
+// A source is called once per particle p: it performs the particle update
+// (if any), fills the particle's cell and its NCH deposit values (scaled by
+// 2^E), and returns whether the particle deposits at all.
 
-// Paint particle positions (disp + rsd * mom along rsd_axis) with unit weight.
-template <typename T>
-__global__ void k_paint(Geo g, const T *__restrict__ disp, const T *__restrict__ mom, int rsd_axis,
-                        T rsd, unsigned long long *rho, const int *fx_exp) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= g.np) return;
-  T d[3] = {disp[p], disp[g.np + p], disp[2 * g.np + p]};
-  if (rsd_axis >= 0) d[rsd_axis] += rsd * mom[rsd_axis * g.np + p];
-  const Cell<T> c = locate<T>(g.L, p, d[0], d[1], d[2]);
-  deposit<T>(g.L, rho, c, (T)ldexp(1.0, *fx_exp));
-}
+// 2LPT initial conditions: disp = (D1 psi1 + D2 psi2)/Delta,
+// mom = (Gp1 psi1 + Gp2 psi2)/Delta (cell units); deposit unit weight.
+template <typename T> struct SrcLpt {
+  static constexpr int NCH = 1;
+  Lattice L;
+  int64_t np;
+  const T *psi1, *psi2;
+  T d1, d2, gp1, gp2;
+  T *disp, *mom;
+  const int *fx_exp;  // null: no deposit
+  T scale;
+  __device__ void setup() { scale = fx_exp ? (T)ldexp(1.0, __ldg(fx_exp)) : T(0); }
+  __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
+    T d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T a1 = psi1[a * np + p];
+      const T a2 = psi2 ? psi2[a * np + p] : T(0);
+      d[a] = d1 * a1 + d2 * a2;
+      disp[a * np + p] = d[a];
+      mom[a * np + p] = gp1 * a1 + gp2 * a2;
+    }
+    c = locate<T>(L, p, d[0], d[1], d[2]);
+    v[0] = scale;
+    return fx_exp != nullptr;
+  }
+};
+
+// Positions disp + rsd * mom along rsd_axis (rsd_axis < 0: none), unit weight.
+template <typename T> struct SrcPaint {
+  static constexpr int NCH = 1;
+  Lattice L;
+  int64_t np;
+  const T *disp, *mom;
+  int rsd_axis;
+  T rsd;
+  const int *fx_exp;
+  T scale;
+  __device__ void setup() { scale = (T)ldexp(1.0, __ldg(fx_exp)); }
+  __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
+    T d[3] = {disp[p], disp[np + p], disp[2 * np + p]};
+    if (rsd_axis >= 0) d[rsd_axis] += rsd * mom[rsd_axis * np + p];
+    c = locate<T>(L, p, d[0], d[1], d[2]);
+    v[0] = scale;
+    return true;
+  }
+};
 
 // One fused leapfrog update: F = readout(Phi, x); p += kick F; x' = x + drift p;
-// paint x' (if rho).  x and x' may alias.
-template <typename T>
-__global__ void k_kdk(Geo g, const V4<T> *__restrict__ phi, const T *x, T *xn, T *__restrict__ mom,
-                      T kick, T drift, unsigned long long *rho, const int *fx_exp) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= g.np) return;
-  const T x0 = x[p], x1 = x[g.np + p], x2 = x[2 * g.np + p];
-  Cell<T> c = locate<T>(g.L, p, x0, x1, x2);
-  T f0, f1, f2;
-  readout3<T>(g.L, phi, c, f0, f1, f2);
-  const T p0 = mom[p] + kick * f0, p1 = mom[g.np + p] + kick * f1, p2 = mom[2 * g.np + p] + kick * f2;
-  mom[p] = p0;
-  mom[g.np + p] = p1;
-  mom[2 * g.np + p] = p2;
-  const T y0 = x0 + drift * p0, y1 = x1 + drift * p1, y2 = x2 + drift * p2;
-  xn[p] = y0;
-  xn[g.np + p] = y1;
-  xn[2 * g.np + p] = y2;
-  if (rho) {
-    c = locate<T>(g.L, p, y0, y1, y2);
-    deposit<T>(g.L, rho, c, (T)ldexp(1.0, *fx_exp));
+// deposit x'.  x and x' may alias.
+template <typename T> struct SrcKdk {
+  static constexpr int NCH = 1;
+  Lattice L;
+  int64_t np;
+  const V4<T> *phi;
+  const T *x;
+  T *xn, *mom;
+  T kick, drift;
+  const int *fx_exp;
+  T scale;
+  __device__ void setup() { scale = (T)ldexp(1.0, __ldg(fx_exp)); }
+  __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
+    const T x0 = x[p], x1 = x[np + p], x2 = x[2 * np + p];
+    c = locate<T>(L, p, x0, x1, x2);
+    T f0, f1, f2;
+    readout3<T>(L, phi, c, f0, f1, f2);
+    const T p0 = mom[p] + kick * f0, p1 = mom[np + p] + kick * f1, p2 = mom[2 * np + p] + kick * f2;
+    mom[p] = p0;
+    mom[np + p] = p1;
+    mom[2 * np + p] = p2;
+    const T y0 = x0 + drift * p0, y1 = x1 + drift * p1, y2 = x2 + drift * p2;
+    xn[p] = y0;
+    xn[np + p] = y1;
+    xn[2 * np + p] = y2;
+    c = locate<T>(L, p, y0, y1, y2);
+    v[0] = scale;
+    return true;
   }
-}
+};
 
-// Last half kick p += kick F(x), then paint x + rsd * p along rsd_axis.
-template <typename T>
-__global__ void k_final(Geo g, const V4<T> *__restrict__ phi, const T *__restrict__ x, T *__restrict__ mom,
-                        T kick, int rsd_axis, T rsd, unsigned long long *rho, const int *fx_exp) {
+// Last half kick p += kick F(x), then deposit x + rsd * p along rsd_axis
+// (fx_exp null: kick only).
+template <typename T> struct SrcFinal {
+  static constexpr int NCH = 1;
+  Lattice L;
+  int64_t np;
+  const V4<T> *phi;
+  const T *x;
+  T *mom;
+  T kick;
+  int rsd_axis;
+  T rsd;
+  const int *fx_exp;
+  T scale;
+  __device__ void setup() { scale = fx_exp ? (T)ldexp(1.0, __ldg(fx_exp)) : T(0); }
+  __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
+    T d[3] = {x[p], x[np + p], x[2 * np + p]};
+    c = locate<T>(L, p, d[0], d[1], d[2]);
+    T f[3];
+    readout3<T>(L, phi, c, f[0], f[1], f[2]);
+    T m[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      m[a] = mom[a * np + p] + kick * f[a];
+      mom[a * np + p] = m[a];
+    }
+    if (rsd_axis >= 0) d[rsd_axis] += rsd * m[rsd_axis];
+    c = locate<T>(L, p, d[0], d[1], d[2]);
+    v[0] = scale;
+    return fx_exp != nullptr;
+  }
+};
+
+// 3-channel force cotangent c_k * pbar at x_k, fixed point with the exponent
+// chosen from the running max of |c_k pbar| (written to fx_exp_out).
+template <typename T> struct SrcAdj3 {
+  static constexpr int NCH = 3;
+  Lattice L;
+  int64_t np;
+  int log2np;
+  const T *x, *pbar;
+  T ck;
+  const unsigned long long *maxslot;
+  int *fx_exp_out;
+  int e;
+  __device__ void setup() {
+    e = fixed_exponent((double)read_max_abs<T>(maxslot), log2np);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *fx_exp_out = e;
+  }
+  __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[3]) const {
+    c = locate<T>(L, p, x[p], x[np + p], x[2 * np + p]);
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T w = ck * pbar[a * np + p];
+      if constexpr (sizeof(T) == 4) w = scalbnf(w, e);
+      else w = scalbn(w, e);
+      v[a] = w;
+      any |= (w != T(0));
+    }
+    return any;
+  }
+};
+
+// ---- deposition launch ----------------------------------------------------
+// One thread per particle, in lattice order (a warp covers 32 consecutive
+// particles along the fastest lattice axis, so its loads are coalesced and
+// its deposits land in neighbouring cells).  Deposits are integer atomics of
+// q = rint(w v), so the mesh is the same for every schedule.
+template <typename T, class Src>
+__global__ void __launch_bounds__(256) k_deposit(Geo g, Src src, unsigned long long *mesh, int64_t plane) {
+  constexpr int NCH = Src::NCH;
+  Src s = src;
+  s.setup();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= g.np) return;
-  T d[3] = {x[p], x[g.np + p], x[2 * g.np + p]};
-  Cell<T> c = locate<T>(g.L, p, d[0], d[1], d[2]);
-  T f[3];
-  readout3<T>(g.L, phi, c, f[0], f[1], f[2]);
-  T m[3];
+  Cell<T> c;
+  T v[NCH];
+  if (!s(p, c, v)) return;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    m[a] = mom[a * g.np + p] + kick * f[a];
-    mom[a * g.np + p] = m[a];
-  }
-  if (rho) {
-    if (rsd_axis >= 0) d[rsd_axis] += rsd * m[rsd_axis];
-    c = locate<T>(g.L, p, d[0], d[1], d[2]);
-    deposit<T>(g.L, rho, c, (T)ldexp(1.0, *fx_exp));
-  }
+  for (int ch = 0; ch < NCH; ++ch)
+    if (v[ch] != T(0)) deposit<T>(g.L, mesh + ch * plane, c, v[ch]);
 }
 
 // Plain readout of the force (probe): out = Delta * F at x.
@@ -285,26 +379,6 @@ __global__ void k_adj_final(Geo g, const T *__restrict__ x, const T *__restrict_
   // warp max then one atomic per warp
   for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) atomic_max_abs<T>(maxslot, mx);
-}
-
-// 3-channel paint of the force cotangent c_k * pbar at x_k, fixed point with
-// the exponent chosen from the running max.
-template <typename T>
-__global__ void k_adj_paint3(Geo g, const T *__restrict__ x, const T *__restrict__ pbar, T ck,
-                             unsigned long long *m3, const unsigned long long *maxslot, int *fx_exp_out) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int e = fixed_exponent((double)read_max_abs<T>(maxslot), g.log2np);
-  if (p == 0) *fx_exp_out = e;
-  if (p >= g.np) return;
-  const Cell<T> c = locate<T>(g.L, p, x[p], x[g.np + p], x[2 * g.np + p]);
-  const int64_t m = (int64_t)g.np;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    T v = ck * pbar[a * g.np + p];
-    if constexpr (sizeof(T) == 4) v = scalbnf(v, e);
-    else v = scalbn(v, e);
-    if (v != T(0)) deposit<T>(g.L, m3 + a * m, c, v);
-  }
 }
 
 // Adjoint gather at x_k: xbar += grad_u sum W (c_k pbar . Phi_k + rhobar);

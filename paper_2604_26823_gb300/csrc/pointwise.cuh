@@ -100,7 +100,7 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T delta;
-    if constexpr (sizeof(T) == 4) delta = scalbnf(__ll2float_rn(rho[i]), e) - 1.0f;
+    if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i]), e) - 1.0f;
     else delta = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
     if (delta_out) delta_out[i] = delta;
     const T r = resp[i];
@@ -134,7 +134,7 @@ __global__ void k_expected(LossParams lp, const long long *__restrict__ rho, con
   if (i >= n) return;
   const int e = -__ldg(fx_exp);
   T delta;
-  if constexpr (sizeof(T) == 4) delta = scalbnf(__ll2float_rn(rho[i]), e) - 1.0f;
+  if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i]), e) - 1.0f;
   else delta = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
   if (lp.lik == 0) {
     out[i] = (T)lp.b * delta;
@@ -182,7 +182,7 @@ __global__ void k_fixed_to_delta(const long long *__restrict__ rho, const int *f
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int e = -__ldg(fx_exp);
-  if constexpr (sizeof(T) == 4) out[i] = scalbnf(__ll2float_rn(rho[i]), e) - 1.0f;
+  if constexpr (sizeof(T) == 4) out[i] = scalbnf(fx_i64_to_f32(rho[i]), e) - 1.0f;
   else out[i] = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
 }
 
