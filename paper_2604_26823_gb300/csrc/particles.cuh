@@ -49,36 +49,10 @@ __device__ __forceinline__ int64_t mesh_index(const Lattice &L, int x, int y, in
   return ((((int64_t)x) << L.logn | y) << L.logn) | z;
 }
 
-// The 8 CIC deposits of weight v (already scaled by 2^E) as integers
-// q = rint(w * v), handed to f(ox, oy, oz, q) for every non-zero q.  Every
-// deposit path rounds through this one expression, so they agree bit for bit.
-template <typename T, class F>
-__device__ __forceinline__ void cic_corners(const Cell<T> &c, T v, F &&f) {
-  const T wx[2] = {T(1) - c.f[0], c.f[0]};
-  const T wy[2] = {T(1) - c.f[1], c.f[1]};
-  const T wz[2] = {T(1) - c.f[2], c.f[2]};
-#pragma unroll
-  for (int ox = 0; ox < 2; ++ox)
-#pragma unroll
-    for (int oy = 0; oy < 2; ++oy) {
-      const T wxy = wx[ox] * wy[oy] * v;
-#pragma unroll
-      for (int oz = 0; oz < 2; ++oz) {
-        const T w = wxy * wz[oz];
-        long long q;
-        if constexpr (sizeof(T) == 4) q = fx_f32_to_i64(w);
-        else q = __double2ll_rn(w);
-        if (q) f(ox, oy, oz, q);
-      }
-    }
-}
-
-// Deposit onto the 8 nodes with global integer atomics.
-template <typename T>
-__device__ __forceinline__ void deposit(const Lattice &L, unsigned long long *mesh, const Cell<T> &c, T v) {
-  cic_corners<T>(c, v, [&](int ox, int oy, int oz, long long q) {
-    fx_add(mesh + mesh_index(L, (c.c[0] + ox) & L.mask, (c.c[1] + oy) & L.mask, (c.c[2] + oz) & L.mask), q);
-  });
+// A deposit rint(w) of a weight already scaled by 2^E, as an integer.
+template <typename T> __device__ __forceinline__ long long fx_round(T w) {
+  if constexpr (sizeof(T) == 4) return fx_f32_to_i64(w);
+  else return __double2ll_rn(w);
 }
 
 // F = sum_c W(u - c) Phi(c) over a 4-component mesh (x, y, z used).
@@ -319,23 +293,57 @@ template <typename T> struct SrcAdj3 {
 };
 
 // ---- deposition launch ----------------------------------------------------
-// One thread per particle, in lattice order (a warp covers 32 consecutive
-// particles along the fastest lattice axis, so its loads are coalesced and
-// its deposits land in neighbouring cells).  Deposits are integer atomics of
-// q = rint(w v), so the mesh is the same for every schedule.
+// One thread per particle, in lattice order: a warp covers 32 consecutive
+// particles along the fastest lattice axis (z), so its loads are coalesced.
+// Each particle's 8 CIC deposits are integers q = rint(w v) added with
+// integer atomics, so the mesh is the same for every schedule.
+//
+// Warp merge along z: when the next lane's particle has the same (x, y) cell
+// and the z cell above (the usual case away from shell crossing), its four
+// lower-z deposits land on this lane's four upper-z nodes; they are passed
+// down by a shuffle and added here, so that lane issues only its upper-z
+// atomics.  The merged sums are sums of the same integers, so the mesh is
+// unchanged bit for bit, with up to half the atomics.
 template <typename T, class Src>
 __global__ void __launch_bounds__(256) k_deposit(Geo g, Src src, unsigned long long *mesh, int64_t plane) {
   constexpr int NCH = Src::NCH;
+  constexpr unsigned kFull = 0xffffffffu;
   Src s = src;
   s.setup();
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= g.np) return;
-  Cell<T> c;
-  T v[NCH];
-  if (!s(p, c, v)) return;
+  Cell<T> c{};
+  T v[NCH] = {};
+  bool live = false;
+  if (p < g.np) live = s(p, c, v);
+  const int mask = g.L.mask, lane = threadIdx.x & 31;
+  const int cx = live ? c.c[0] : -1, cy = live ? c.c[1] : -1, cz = live ? c.c[2] : -1;
+  const int ux = __shfl_down_sync(kFull, cx, 1), uy = __shfl_down_sync(kFull, cy, 1);
+  const int uz = __shfl_down_sync(kFull, cz, 1);
+  const bool merge_up = live && lane < 31 && ux == cx && uy == cy && uz == ((cz + 1) & mask);
+  const bool merged_down = __shfl_up_sync(kFull, merge_up ? 1 : 0, 1) != 0 && lane > 0;
+  const T wx[2] = {T(1) - c.f[0], c.f[0]};
+  const T wy[2] = {T(1) - c.f[1], c.f[1]};
+  const T wz[2] = {T(1) - c.f[2], c.f[2]};
+  const int xs[2] = {cx, (cx + 1) & mask}, ys[2] = {cy, (cy + 1) & mask};
+  const int z1 = (cz + 1) & mask;
 #pragma unroll
-  for (int ch = 0; ch < NCH; ++ch)
-    if (v[ch] != T(0)) deposit<T>(g.L, mesh + ch * plane, c, v[ch]);
+  for (int ch = 0; ch < NCH; ++ch) {
+#pragma unroll
+    for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy) {
+        const T wxy = wx[ox] * wy[oy] * v[ch];
+        long long q0 = live ? fx_round<T>(wxy * wz[0]) : 0;
+        long long q1 = live ? fx_round<T>(wxy * wz[1]) : 0;
+        const long long up0 = __shfl_down_sync(kFull, q0, 1);
+        if (merge_up) q1 += up0;
+        if (live) {
+          unsigned long long *col = mesh + ch * plane + ((((int64_t)xs[ox]) << g.L.logn | ys[oy]) << g.L.logn);
+          if (q0 && !merged_down) fx_add(col + cz, q0);
+          if (q1) fx_add(col + z1, q1);
+        }
+      }
+  }
 }
 
 // Plain readout of the force (probe): out = Delta * F at x.
