@@ -37,27 +37,9 @@ N, BOX, STEPS_PM = 256, 500.0, 10
 NBAR = 1e-3
 ROM_EVERY = 20
 
-def mock_inputs(api, inputs, plan1_cfg, lnk, lnp, rank):
-    """Selection R, mock counts N_G ~ Poisson(lambda(s_true)) and the start s0."""
-    import torch
-    dev = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
-    R = inputs.survey_selection(N, BOX, seed=4)
-    s_true = inputs.white_noise(N, 1 + 1000 * rank)
-    # normalisation: nbar_cell = nbar Delta^3 / mean_box[(1+delta)^alpha sigmoid(...)]
-    probe = api.Plan(plan1_cfg, lnk, lnp)
-    ones = dev(np.ones((N, N, N), np.float32))
-    g = api.pm_expected_counts(probe, dev(s_true), ones)
-    mean_g = float(g.cpu().numpy().astype(np.float64).mean())
-    del probe, g, ones
-    torch.cuda.empty_cache()
-    nbar_cell = NBAR * (BOX / N) ** 3 / mean_g
-    return R, s_true, nbar_cell
-
-
 def config(api, nbar_cell, precision="f32"):
-    return api.Config(n=N, box=BOX, n_steps=STEPS_PM, lpt_order=2, rsd_axis=-1, likelihood="poisson",
-                      precision=precision, alpha=0.7, delta_th=1.2, K=3.0, nbar_cell=nbar_cell,
-                      rho_floor=1e-3, prior_weight=1.0)
+    from paper_2604_26823_gb300 import recon
+    return recon.mock_config(N, BOX, nbar_cell, precision, n_steps=STEPS_PM)
 
 
 class Clocks:
@@ -172,23 +154,61 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_ckpt512(api, inputs, lnk, lnp, evals=3):
+    """pm_adjoint at 512^3 in a 1000 Mpc/h box, 2LPT + 10 steps, Gaussian
+    likelihood with b = 1.5 over the full box, particle states checkpointed
+    every 2 steps; data is a seeded N(0,1) field (the cost does not depend on
+    its values)."""
+    import torch
+    n = 512
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    free0, total = torch.cuda.mem_get_info()
+    cfg = api.Config(n=n, box=1000.0, n_steps=STEPS_PM, lpt_order=2, rsd_axis=-1, likelihood="gaussian",
+                     bias_b=1.5, sigma=1.0, prior_weight=1.0, checkpoint_every=2)
+    plan = api.Plan(cfg, lnk, lnp)
+    s = torch.from_numpy(inputs.white_noise(n, 1)).cuda()
+    d = torch.from_numpy(inputs.normal_field(n, 3)).cuda()
+    R = torch.ones((n, n, n), dtype=torch.float32, device="cuda")
+    g = torch.empty_like(s)
+    api.pm_adjoint(plan, s, d, R, grad_out=g)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(evals):
+        api.pm_adjoint(plan, s, d, R, grad_out=g)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / evals
+    free1, _ = torch.cuda.mem_get_info()
+    out = {"workload": "ckpt-512", "n_mesh": n, "box": 1000.0, "pm_steps": STEPS_PM, "checkpoint_every": 2,
+           "value": 1e3 / ms, "unit": UNIT, "ms_per_eval": ms, "evals": evals,
+           "workspace_gb": plan.workspace_bytes / 1e9,
+           "peak_torch_allocated_gb": torch.cuda.max_memory_allocated() / 1e9,
+           "device_used_gb": (total - free1) / 1e9}
+    plan.close()
+    del plan, s, d, R, g
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
-    from paper_2604_26823_gb300 import api, build, inputs
+    from paper_2604_26823_gb300 import api, build, inputs, recon
     build.build()
     lib = api.L.load()
     torch.cuda.set_device(local)
     lnk, lnp = api.pm_linear_power_table()
     dev = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
 
-    R_h, s_true, nbar_cell = mock_inputs(api, inputs, config(api, 1.0), lnk, lnp, rank)
+    R_h, s_true, counts_h, nbar_cell = recon.masked_mock(N, BOX, n_steps=STEPS_PM, nbar=NBAR,
+                                                         seed_truth=1 + 1000 * rank, seed_counts=3 + 1000 * rank,
+                                                         lnk=lnk, lnp=lnp)
     cfg = config(api, nbar_cell)
     plan = api.Plan(cfg, lnk, lnp)
     R = dev(R_h)
-    lam = api.pm_expected_counts(plan, dev(s_true), R)
-    counts_h = inputs.poisson_counts(lam.cpu().numpy(), 3 + 1000 * rank)
     counts = dev(counts_h)
-    del lam
     n_gal = float(counts_h.sum())
     vol_frac = float((R_h > 0).mean())
     ncount = api.pm_count_positive(plan, R)
@@ -284,6 +304,15 @@ def run_ours(args, ws, rank, local):
         torch.cuda.empty_cache()
         plan = api.Plan(cfg, lnk, lnp)
 
+    # checkpointed 512^3 configuration (1000 Mpc/h, 10 steps, states kept every
+    # 2 steps): gradient evals/s and peak device memory
+    ck512 = None
+    if not args.no_512:
+        del plan
+        torch.cuda.empty_cache()
+        ck512 = run_ckpt512(api, inputs, lnk, lnp)
+        plan = api.Plan(cfg, lnk, lnp)
+
     # end to end through the public API with pinned host buffers: every step
     # uploads s, the counts and R and reads back the loss
     s_pin = torch.from_numpy(state["s"].cpu().numpy()).pin_memory()
@@ -326,7 +355,7 @@ def run_ours(args, ws, rank, local):
                            "pm_steps": STEPS_PM, "lbfgs_m": 10, "rom_every": ROM_EVERY,
                            "likelihood": "poisson", "galaxies": n_gal, "selection_volume_frac": vol_frac,
                            "parallelism": f"replicas x{ws}", "l2": "working set ~7 GB >> 129 MB L2 (no flush)"},
-                "fp64_path": fp64, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+                "fp64_path": fp64, "checkpointed_512": ck512, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
                 "gpu_launches": int(launches), "clocks": clk, "kernel_classes": classes,
                 "final_loss": losses[-1]}
         print(json.dumps(line), flush=True)
@@ -340,6 +369,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-512", action="store_true", help="skip the checkpointed 512^3 measurement")
     args = ap.parse_args()
     ws, rank, local = (1, 0, 0) if args.impl == "reference" and int(os.environ.get("WORLD_SIZE", "1")) == 1 \
         else dist_setup()

@@ -21,14 +21,13 @@ N = 256
 @pytest.fixture(scope="module")
 def setup():
     import bench
-    from paper_2604_26823_gb300 import api, build, inputs
+    from paper_2604_26823_gb300 import build
     build.build()
+    from paper_2604_26823_gb300 import api, inputs, recon
     lnk, lnp = api.pm_linear_power_table()
-    R, s_true, nbar_cell = bench.mock_inputs(api, inputs, bench.config(api, 1.0), lnk, lnp, 0)
+    R, s_true, counts, nbar_cell = recon.masked_mock(N, bench.BOX, n_steps=bench.STEPS_PM, nbar=bench.NBAR,
+                                                    lnk=lnk, lnp=lnp)
     plan32 = api.Plan(bench.config(api, nbar_cell, "f32"), lnk, lnp)
-    dev32 = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
-    lam = api.pm_expected_counts(plan32, dev32(s_true), dev32(R))
-    counts = inputs.poisson_counts(lam.cpu().numpy(), 3)
     s0 = inputs.white_noise(N, 2)
     return dict(api=api, bench=bench, lnk=lnk, lnp=lnp, R=R, counts=counts, s0=s0, nbar=nbar_cell,
                 plan32=plan32)
