@@ -23,17 +23,28 @@ template <typename T> struct FftCfg {
   static constexpr int B = sizeof(T) == 4 ? 16 : 8;
 };
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
 template <typename T, int N> struct ZCfg {
   static constexpr int B = FftCfg<T>::B;
   static constexpr int LEN = N / 2;
   static constexpr int NT = cmin(N == 512 ? 512 : 256, B * LEN);
   static constexpr size_t SMEM = (size_t)LEN * (B + 1) * sizeof(cx<T>);
+  // FP32, 256-thread tiles: CTAs per SM the c2r pass with NIN inputs can
+  // hold by shared memory (up to 3); its register budget is capped to match,
+  // so registers do not set a lower occupancy than shared memory does.  The
+  // FP64 and 512-thread variants keep the full budget (they would spill).
+  template <int NIN> static constexpr int minb() {
+    return (sizeof(T) == 4 && NT <= 256) ? cmax(1, cmin(3, (int)((227u * 1024u) / (NIN * SMEM)))) : 1;
+  }
 };
 template <typename T, int N> struct CCfg {
   static constexpr int B = FftCfg<T>::B;
   static constexpr int NT = cmin(N == 512 ? 512 : 256, B * N);
   static constexpr size_t SMEM = (size_t)N * B * sizeof(cx<T>);
   static constexpr size_t SMEM2 = 2 * SMEM;  // fused x pass: two tiles
+  // FP32, 256-thread tiles: CTAs per SM of the fused x pass by shared
+  // memory (up to 3), as a floor for the register budget
+  static constexpr int MINB_X = (sizeof(T) == 4 && NT <= 256) ? cmax(1, cmin(3, (int)((227u * 1024u) / SMEM2))) : 1;
 };
 
 #define PM_DISPATCH_N(nval, ...)             \
@@ -335,7 +346,7 @@ template <typename T> struct Engine {
     ProfScope ps(prof, P_X_FUSED, st, (double)(1 + count) * S * sizeof(C));
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
-      auto kern = fft::k_x_1toM<T, NN, CC::B, CC::NT>;
+      auto kern = fft::k_x_1toM<T, NN, CC::B, CC::NT, CC::MINB_X>;
       set_smem(kern, CC::SMEM2);
       ::pm::note_launch();
       kern<<<(int)(S / n / CC::B), CC::NT, CC::SMEM2, st>>>(a, tw);
@@ -356,7 +367,7 @@ template <typename T> struct Engine {
     ProfScope ps(prof, P_X_FUSED, st, (double)(1 + count) * S * sizeof(C));
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
-      auto kern = fft::k_x_Mto1<T, NN, CC::B, CC::NT>;
+      auto kern = fft::k_x_Mto1<T, NN, CC::B, CC::NT, CC::MINB_X>;
       set_smem(kern, CC::SMEM2);
       ::pm::note_launch();
       kern<<<(int)(S / n / CC::B), CC::NT, CC::SMEM2, st>>>(a, tw);
@@ -370,7 +381,7 @@ template <typename T> struct Engine {
     ProfScope ps(prof, P_Z_C2R, st, (double)nb * NIN * S * sizeof(C) + (double)nb * M * Out::kWriteBytes);
     PM_DISPATCH_N(n, {
       using Z = ZCfg<T, NN>;
-      auto kern = fft::k_z_c2r<T, NN, Z::B, Z::NT, NIN, Out>;
+      auto kern = fft::k_z_c2r<T, NN, Z::B, Z::NT, NIN, Out, Z::template minb<NIN>()>;
       set_smem(kern, NIN * Z::SMEM);
       ::pm::note_launch();
       kern<<<(int)((int64_t)nb * n * n / Z::B), Z::NT, NIN * Z::SMEM, st>>>(ins, out, tw);

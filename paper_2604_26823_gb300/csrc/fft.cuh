@@ -332,8 +332,8 @@ struct XArgsN {  // up to 9 input spectra -> one output spectrum
 
 // x pass, case "one to many": X = FFT_x(in); out_o = IFFT_x(h_o X), o < count.
 // Shared memory holds the transformed input (kept) and one work tile.
-template <typename T, int N, int B, int NT>
-__global__ void __launch_bounds__(NT) k_x_1toM(XArgs1 a, const cx<T> *__restrict__ tw) {
+template <typename T, int N, int B, int NT, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) k_x_1toM(XArgs1 a, const cx<T> *__restrict__ tw) {
   using C = cx<T>;
   constexpr int H = N / 2 + 1;
   static_assert(N * B % NT == 0, "tile must split evenly over threads");
@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(NT) k_x_1toM(XArgs1 a, const cx<T> *__restrict
 
 // x pass, case "many to one": out = IFFT_x( sum_i h_i FFT_x(in_i) ).
 // Shared memory holds one work tile and the accumulator.
-template <typename T, int N, int B, int NT>
-__global__ void __launch_bounds__(NT) k_x_Mto1(XArgsN a, const cx<T> *__restrict__ tw) {
+template <typename T, int N, int B, int NT, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) k_x_Mto1(XArgsN a, const cx<T> *__restrict__ tw) {
   using C = cx<T>;
   constexpr int H = N / 2 + 1;
   static_assert(N * B % NT == 0, "tile must split evenly over threads");
@@ -401,8 +401,8 @@ struct Ins {
 // z pass, half complex -> real (unnormalised) for NIN spectra sharing rows;
 // Out::put(row, m, v[NIN]) receives the real pair (x_{2m}, x_{2m+1}) of each.
 // Each input is transformed in its own shared-memory tile.
-template <typename T, int N, int B, int NT, int NIN, class Out>
-__global__ void __launch_bounds__(NT) k_z_c2r(Ins ins, Out out, const cx<T> *__restrict__ tw) {
+template <typename T, int N, int B, int NT, int NIN, class Out, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) k_z_c2r(Ins ins, Out out, const cx<T> *__restrict__ tw) {
   using C = cx<T>;
   constexpr int LEN = N / 2;
   constexpr int SB = B + 1;

@@ -49,6 +49,15 @@ __device__ __forceinline__ int64_t mesh_index(const Lattice &L, int x, int y, in
   return ((((int64_t)x) << L.logn | y) << L.logn) | z;
 }
 
+// 2^e for the unit-weight deposit scale (e = 61 - log2(np) - 1 lies in
+// [33, 48] for 512^3 .. 16^3 particles, inside the float exponent range);
+// built from the exponent bits, since a double ldexp would issue on the
+// narrow FP64 unit.
+template <typename T> __device__ __forceinline__ T pow2(int e) {
+  if constexpr (sizeof(T) == 4) return __int_as_float((e + 127) << 23);
+  else return ldexp(1.0, e);
+}
+
 // A deposit rint(w) of a weight already scaled by 2^E, as an integer.
 template <typename T> __device__ __forceinline__ long long fx_round(T w) {
   if constexpr (sizeof(T) == 4) return fx_f32_to_i64(w);
@@ -159,7 +168,7 @@ template <typename T> struct SrcLpt {
   T *disp, *mom;
   const int *fx_exp;  // null: no deposit
   T scale;
-  __device__ void setup() { scale = fx_exp ? (T)ldexp(1.0, __ldg(fx_exp)) : T(0); }
+  __device__ void setup() { scale = fx_exp ? pow2<T>(__ldg(fx_exp)) : T(0); }
   __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
     T d[3];
 #pragma unroll
@@ -186,7 +195,7 @@ template <typename T> struct SrcPaint {
   T rsd;
   const int *fx_exp;
   T scale;
-  __device__ void setup() { scale = (T)ldexp(1.0, __ldg(fx_exp)); }
+  __device__ void setup() { scale = pow2<T>(__ldg(fx_exp)); }
   __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
     T d[3] = {disp[p], disp[np + p], disp[2 * np + p]};
     if (rsd_axis >= 0) d[rsd_axis] += rsd * mom[rsd_axis * np + p];
@@ -208,7 +217,7 @@ template <typename T> struct SrcKdk {
   T kick, drift;
   const int *fx_exp;
   T scale;
-  __device__ void setup() { scale = (T)ldexp(1.0, __ldg(fx_exp)); }
+  __device__ void setup() { scale = pow2<T>(__ldg(fx_exp)); }
   __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
     const T x0 = x[p], x1 = x[np + p], x2 = x[2 * np + p];
     c = locate<T>(L, p, x0, x1, x2);
@@ -242,7 +251,7 @@ template <typename T> struct SrcFinal {
   T rsd;
   const int *fx_exp;
   T scale;
-  __device__ void setup() { scale = fx_exp ? (T)ldexp(1.0, __ldg(fx_exp)) : T(0); }
+  __device__ void setup() { scale = fx_exp ? pow2<T>(__ldg(fx_exp)) : T(0); }
   __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
     T d[3] = {x[p], x[np + p], x[2 * np + p]};
     c = locate<T>(L, p, d[0], d[1], d[2]);
