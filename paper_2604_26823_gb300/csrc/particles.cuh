@@ -58,10 +58,17 @@ template <typename T> __device__ __forceinline__ T pow2(int e) {
   else return ldexp(1.0, e);
 }
 
-// A deposit rint(w) of a weight already scaled by 2^E, as an integer.
-template <typename T> __device__ __forceinline__ long long fx_round(T w) {
-  if constexpr (sizeof(T) == 4) return fx_f32_to_i64(w);
-  else return __double2ll_rn(w);
+// A deposit rint(w) of a weight already scaled by 2^E, as an integer.  For
+// FP32 the two exact round-to-nearest conversions run on different units
+// (HW: the hardware conversion, on the FP64 unit; otherwise integer
+// operations): the deposit kernel alternates them so neither unit limits it.
+template <typename T, bool HW> __device__ __forceinline__ long long fx_round(T w) {
+  if constexpr (sizeof(T) == 4) {
+    if constexpr (HW) return __float2ll_rn(w);
+    else return fx_f32_to_i64(w);
+  } else {
+    return __double2ll_rn(w);
+  }
 }
 
 // F = sum_c W(u - c) Phi(c) over a 4-component mesh (x, y, z used).
@@ -142,6 +149,13 @@ __device__ __forceinline__ int fixed_exponent(double maxabs, int log2_particles)
   int e;
   frexp(maxabs, &e);  // maxabs < 2^e
   return 61 - log2_particles - e;
+}
+// The same from the running max held as the bits of a non-negative float
+// (read_max_abs<float>), without FP64 arithmetic for normal numbers.
+__device__ __forceinline__ int fixed_exponent_f32(unsigned bits, int log2_particles) {
+  const int be = (int)(bits >> 23);
+  if (bits == 0u || be == 0) return fixed_exponent((double)__uint_as_float(bits), log2_particles);
+  return 61 - log2_particles - (be - 126);  // maxabs = m 2^(be - 126), m in [0.5, 1)
 }
 
 // ---- kernels ------------------------------------------------------------
@@ -283,7 +297,8 @@ template <typename T> struct SrcAdj3 {
   int *fx_exp_out;
   int e;
   __device__ void setup() {
-    e = fixed_exponent((double)read_max_abs<T>(maxslot), log2np);
+    if constexpr (sizeof(T) == 4) e = fixed_exponent_f32(*reinterpret_cast<const unsigned *>(maxslot), log2np);
+    else e = fixed_exponent((double)read_max_abs<T>(maxslot), log2np);
     if (blockIdx.x == 0 && threadIdx.x == 0) *fx_exp_out = e;
   }
   __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[3]) const {
@@ -314,7 +329,7 @@ template <typename T> struct SrcAdj3 {
 // atomics.  The merged sums are sums of the same integers, so the mesh is
 // unchanged bit for bit, with up to half the atomics.
 template <typename T, class Src>
-__global__ void __launch_bounds__(256) k_deposit(Geo g, Src src, unsigned long long *mesh, int64_t plane) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_deposit(Geo g, Src src, unsigned long long *mesh, int64_t plane) {
   constexpr int NCH = Src::NCH;
   constexpr unsigned kFull = 0xffffffffu;
   Src s = src;
@@ -342,8 +357,8 @@ __global__ void __launch_bounds__(256) k_deposit(Geo g, Src src, unsigned long l
 #pragma unroll
       for (int oy = 0; oy < 2; ++oy) {
         const T wxy = wx[ox] * wy[oy] * v[ch];
-        long long q0 = live ? fx_round<T>(wxy * wz[0]) : 0;
-        long long q1 = live ? fx_round<T>(wxy * wz[1]) : 0;
+        long long q0 = live ? fx_round<T, true>(wxy * wz[0]) : 0;
+        long long q1 = live ? fx_round<T, false>(wxy * wz[1]) : 0;
         const long long up0 = __shfl_down_sync(kFull, q0, 1);
         if (merge_up) q1 += up0;
         if (live) {

@@ -7,7 +7,7 @@
 // step needs lives in a file-scope device array of the library instead.
 //
 // Scratch: one FP64 partial sum per 4096 elements (at most kMaxBlocks), plus
-// the mean, the sum of squared deviations and the reset counter.  Every GPU
+// the sum, the sum of squared deviations, the reset counter and mu, sd, 1/sd.  Every GPU
 // that loads the library holds this array (about 512 KB) until the process
 // exits.  Every call shares it and it keeps the last call's contents; the
 // reset counter is cleared at the start of each call.  Calls that overlap on
@@ -27,7 +27,7 @@ namespace {
 constexpr int kItems = 4096;                                  // elements per partial sum
 constexpr int64_t kMaxBlocks = 65536;                         // partial sums in the array
 constexpr int64_t kMaxElems = kMaxBlocks * (int64_t)kItems;   // 2^28 elements
-constexpr int kTail = 8;                                      // mean, sum of squares, counter, spare
+constexpr int kTail = 8;                                      // sums, counter, mu / sd / 1/sd, spare
 
 static __device__ __align__(256) double g_project_scratch[kMaxBlocks + kTail];
 
@@ -98,7 +98,9 @@ pm_status run(int64_t n, T *s, uint64_t seed, uint64_t counter, int64_t *n_reset
   pm::pw::k_sum_partials<<<1, pm::pw::kRedThreads, 0, st>>>(partial, blocks, res + 1);
   const unsigned long long key = pm::rom::mix64(seed + counter * pm::rom::kGolden + pm::rom::kGolden);
   ::pm::note_launch();
-  pm::rom::k_project<T><<<pm::grid_for(n, 256), 256, 0, st>>>(s, n, res + 0, res + 1, 10.0, key, cnt);
+  pm::rom::k_project_scalars<<<1, 1, 0, st>>>(n, res + 0, res + 1, res + 3);
+  ::pm::note_launch();
+  pm::rom::k_project<T><<<pm::grid_for(n, 256), 256, 0, st>>>(s, n, res + 3, 10.0, key, cnt);
   PM_LAUNCH_CHECK();
   double h[3];
   PM_CUDA_TRY(cudaMemcpyAsync(h, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -47,20 +47,37 @@ __global__ void k_moment(const T *__restrict__ x, int64_t n, const double *mean_
   pw::block_sum_store(acc, partial);
 }
 
-// s_hat = (s - mu)/sd in FP64; |s_hat| > s_th -> counter-based N(0,1).
-template <typename T>
-__global__ void k_project(T *s, int64_t n, const double *sum, const double *sumsq_dev, double s_th,
-                          unsigned long long key, unsigned long long *nreset) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Projection scalars once: mu, sd and 1/sd (FP64) from the two FP64 sums.
+static __global__ void k_project_scalars(int64_t n, const double *sum, const double *sumsq_dev, double *out3) {
   const double mu = *sum / (double)n;
   const double sd = sqrt(*sumsq_dev / (double)n);
-  double z = ((double)s[i] - mu) / sd;
-  if (fabs(z) > s_th) {
-    z = counter_normal(key, (unsigned long long)i);
-    atomicAdd(nreset, 1ull);
+  out3[0] = mu;
+  out3[1] = sd;
+  out3[2] = 1.0 / sd;
+}
+
+// s_hat = (s - mu)/sd; |s_hat| > s_th -> counter-based N(0,1).  The value is
+// formed as (s - mu) * (1/sd) in T (within an ulp of T of the FP64 quotient,
+// without an FP64 division per element on the narrow FP64 unit); the reset
+// decision is taken on the FP64 quotient itself, evaluated for the elements
+// whose fast value lies within 1e-4 of the threshold, so the set of reset
+// elements is the FP64 rule's.
+template <typename T>
+__global__ void k_project(T *s, int64_t n, const double *scal, double s_th, unsigned long long key,
+                          unsigned long long *nreset) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T mu = (T)scal[0], inv = (T)scal[2];
+  const T v = s[i];
+  T z = (v - mu) * inv;
+  if (fabs((double)z) > s_th * (1.0 - 1e-4)) {
+    const double zd = ((double)v - scal[0]) / scal[1];
+    if (fabs(zd) > s_th) {
+      z = (T)counter_normal(key, (unsigned long long)i);
+      atomicAdd(nreset, 1ull);
+    }
   }
-  s[i] = (T)z;
+  s[i] = z;
 }
 
 template <typename T> __global__ void k_count_pos(const T *__restrict__ R, int64_t n, double *partial) {
@@ -321,7 +338,9 @@ template <typename T> struct Rom {
     PM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), E.st));
     const unsigned long long key = mix64(seed + counter * kGolden + kGolden);
     ::pm::note_launch();
-    k_project<T><<<grid_for(n, 256), 256, 0, E.st>>>(s, n, res + 2, res + 3, 10.0, key, cnt);
+    k_project_scalars<<<1, 1, 0, E.st>>>(n, res + 2, res + 3, res + 6);
+    ::pm::note_launch();
+    k_project<T><<<grid_for(n, 256), 256, 0, E.st>>>(s, n, res + 6, 10.0, key, cnt);
     PM_LAUNCH_CHECK();
     double h[3];
     PM_CUDA_TRY(cudaMemcpyAsync(h, res + 2, 3 * sizeof(double), cudaMemcpyDeviceToHost, E.st));
