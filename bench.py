@@ -36,6 +36,11 @@ UNIT = "gradient evals/s"
 N, BOX, STEPS_PM = 256, 500.0, 10
 NBAR = 1e-3
 ROM_EVERY = 20
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# over the launches of one gradient evaluation of this workload) from one ncu
+# capture of the kernel as it stands; profiles/deposit_traffic_masked_recon_256.md
+# gives the command.  Set to None when the kernel changes.
+NCU_TRAFFIC = {"adj_paint": 1084.2e6}
 
 def config(api, nbar_cell, precision="f32"):
     from paper_2604_26823_gb300 import recon
@@ -261,7 +266,7 @@ def run_ours(args, ws, rank, local):
 
     # dominant kernel class: algorithmic bytes (recorded per launch by the
     # library) over its event-timed duration, against the measured HBM peak
-    peak, peak_src = 6800.0, "fallback"
+    peak, peak_src = 6800.0, "fallback (6.8 TB/s)"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             peak, peak_src = float(json.load(fh)["hbm_gbs"]), "measured"
@@ -275,7 +280,7 @@ def run_ours(args, ws, rank, local):
     if dom_n:
         achieved = dom_b / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_src, "launches": dom_n,
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "peak_source": peak_src, "launches": dom_n,
                 "mean_launch_ms": dom_ms / dom_n, "algorithmic_bytes_per_launch": dom_b / dom_n,
                 "share_of_step": dom_ms / ms}
     # FP64 path: same workload and schedule

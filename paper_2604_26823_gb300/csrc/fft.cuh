@@ -176,6 +176,33 @@ __device__ __forceinline__ ModeK<T> mode_k(int ix, int iy, int iz, int n, T kf) 
   return m;
 }
 
+// The x pass gives each thread one fixed column (iy, iz) of its tile, so the
+// column part of the mode is formed once per thread and only the x part per
+// element (same arithmetic as mode_k).
+template <typename T> struct ColMode {
+  T ky, kz, kf;
+  int nyz2, h, n;
+  __device__ __forceinline__ void init(int iy, int iz, int n_, T kf_) {
+    n = n_;
+    h = n >> 1;
+    kf = kf_;
+    const int ny = iy < h ? iy : iy - n;
+    ky = (iy == h) ? T(0) : kf * (T)ny;
+    kz = (iz == h) ? T(0) : kf * (T)iz;
+    nyz2 = ny * ny + iz * iz;
+  }
+  __device__ __forceinline__ ModeK<T> at(int ix) const {
+    ModeK<T> m;
+    const int nx = ix < h ? ix : ix - n;
+    m.k[0] = (ix == h) ? T(0) : kf * (T)nx;
+    m.k[1] = ky;
+    m.k[2] = kz;
+    const int n2 = nx * nx + nyz2;
+    m.ik2 = n2 > 0 ? T(1) / (kf * kf * (T)n2) : T(0);
+    return m;
+  }
+};
+
 template <typename T, typename C>
 __device__ __forceinline__ C apply_mult(const MultDesc &d, C x, const ModeK<T> &mk, T amp) {
   T f = (T)d.scale;
@@ -303,17 +330,6 @@ __global__ void __launch_bounds__(NT) k_col(const cx<T> *in, cx<T> *out, int64_t
   }
 }
 
-// Per-element mode data of the x pass (pos = ix, column = iy*H + iz).
-template <typename T>
-__device__ __forceinline__ ModeK<T> xpass_mode(int e, int B, int col0, int n, T kf, int64_t &flat) {
-  const int H = n / 2 + 1;
-  const int ix = e / B;
-  const int colg = col0 + e % B;
-  const int iy = colg / H, iz = colg % H;
-  flat = ((int64_t)ix * n + iy) * H + iz;
-  return mode_k<T>(ix, iy, iz, n, kf);
-}
-
 struct XArgs1 {  // one input spectrum -> up to 9 output spectra
   const void *in;
   void *out[9];
@@ -347,12 +363,16 @@ __global__ void __launch_bounds__(NT, MINB) k_x_1toM(XArgs1 a, const cx<T> *__re
                                  [&](int e, C v) { xin[e] = v; });
   __syncthreads();
   smem_fft<C, N, B, B, NT, -1>(xin, tw, 1);
+  static_assert(NT % B == 0, "a thread keeps one column of the tile");
+  const int c = threadIdx.x % B, colg = col0 + c;
+  ColMode<T> cm;
+  cm.init(colg / H, colg % H, N, (T)a.kf);
   for (int o = 0; o < a.mult.count; ++o) {
-    for (int e = threadIdx.x; e < N * B; e += NT) {
-      int64_t flat;
-      const ModeK<T> mk = xpass_mode<T>(e, B, col0, N, (T)a.kf, flat);
-      const T amp = (a.mult.m[o].flags & M_AMP) ? reinterpret_cast<const T *>(a.amp)[flat] : T(0);
-      buf[e] = apply_mult<T, C>(a.mult.m[o], xin[e], mk, amp);
+    const bool use_amp = (a.mult.m[o].flags & M_AMP) != 0;
+    for (int ix = threadIdx.x / B; ix < N; ix += NT / B) {
+      const int e = ix * B + c;
+      const T amp = use_amp ? reinterpret_cast<const T *>(a.amp)[(int64_t)ix * astride + colg] : T(0);
+      buf[e] = apply_mult<T, C>(a.mult.m[o], xin[e], cm.at(ix), amp);
     }
     __syncthreads();
     smem_fft<C, N, B, B, NT, +1>(buf, tw, 1);
@@ -374,17 +394,21 @@ __global__ void __launch_bounds__(NT, MINB) k_x_Mto1(XArgsN a, const cx<T> *__re
   C *acc = buf + N * B;
   const int col0 = blockIdx.x * B;
   const int64_t astride = (int64_t)N * H;
+  static_assert(NT % B == 0, "a thread keeps one column of the tile");
+  const int c = threadIdx.x % B, colg = col0 + c;
+  ColMode<T> cm;
+  cm.init(colg / H, colg % H, N, (T)a.kf);
   for (int i = 0; i < a.mult.count; ++i) {
     const C *src = reinterpret_cast<const C *>(a.in[i]) + col0;
     gather_tile<N * B / NT, NT, C>([&](int e) { return src[(e / B) * astride + e % B]; },
                                    [&](int e, C v) { buf[e] = v; });
     __syncthreads();
     smem_fft<C, N, B, B, NT, -1>(buf, tw, 1);
-    for (int e = threadIdx.x; e < N * B; e += NT) {
-      int64_t flat;
-      const ModeK<T> mk = xpass_mode<T>(e, B, col0, N, (T)a.kf, flat);
-      const T amp = (a.mult.m[i].flags & M_AMP) ? reinterpret_cast<const T *>(a.amp)[flat] : T(0);
-      const C h = apply_mult<T, C>(a.mult.m[i], buf[e], mk, amp);
+    const bool use_amp = (a.mult.m[i].flags & M_AMP) != 0;
+    for (int ix = threadIdx.x / B; ix < N; ix += NT / B) {
+      const int e = ix * B + c;
+      const T amp = use_amp ? reinterpret_cast<const T *>(a.amp)[(int64_t)ix * astride + colg] : T(0);
+      const C h = apply_mult<T, C>(a.mult.m[i], buf[e], cm.at(ix), amp);
       acc[e] = i ? cadd(acc[e], h) : h;
     }
     __syncthreads();
