@@ -260,8 +260,18 @@ template <typename T> struct LoadFixed {
     const longlong2 v = reinterpret_cast<const longlong2 *>(p)[i];
     const int e = -__ldg(exp);
     if constexpr (sizeof(T) == 4) {
-      a = scalbnf(fx_i64_to_f32(v.x), e);
-      b = scalbnf(fx_i64_to_f32(v.y), e);
+      // the two exact int64 -> float conversions run on different units (the
+      // hardware one on the FP64 unit, the other on the integer pipe); the
+      // power-of-two scale is exact for normal results
+      const float fa = __ll2float_rn(v.x), fb = fx_i64_to_f32(v.y);
+      if (e >= -126) {
+        const float sc = __int_as_float((e + 127) << 23);
+        a = fa * sc;
+        b = fb * sc;
+      } else {
+        a = scalbnf(fa, e);
+        b = scalbnf(fb, e);
+      }
     } else {
       a = scalbn(__ll2double_rn(v.x), e);
       b = scalbn(__ll2double_rn(v.y), e);
