@@ -1,7 +1,8 @@
 // L-BFGS two-loop recursion on the GPU (Sec. 2.3.1: the projected L-BFGS
-// step of MujicΛ).  Vectors in the plan precision, every dot product in FP64
-// with a fixed reduction order; the scalars alpha_i stay on the device so
-// the two loops run without host round trips.
+// step of MujicΛ).  Vectors in the plan precision, every dot product with
+// FP64-quality accumulation (pw::DotAcc) and a fixed reduction order; the
+// scalars alpha_i stay on the device so the two loops run without host round
+// trips.
 #include <cmath>
 #include <new>
 #include <vector>
@@ -16,35 +17,76 @@ namespace lb {
 using pw::kRedBlocks;
 using pw::kRedThreads;
 
+// The vector kernels below walk their elements in a grid-stride loop and
+// issue the loads of four strides before using them (the kernels are short
+// and otherwise wait on one load at a time); each thread still visits its
+// elements in increasing order, so every sum is accumulated in the same order
+// as a plain grid-stride loop.
+constexpr int kU = 4;
+
 // s = x_new - x_prev, y = g_new - g_prev into the history slot; x_prev, g_prev
 // updated; block partials of s.y, s.s, y.y.
 template <typename T>
 __global__ void k_pair(const T *__restrict__ xn, const T *__restrict__ gn, T *xp, T *gp, T *__restrict__ sv,
                        T *__restrict__ yv, int64_t n, double *partial) {
-  double a = 0, b = 0, c = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  pw::DotAcc<T> a, b, c;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kU - 1) * st < n; i += kU * st) {
+    T x1[kU], g1[kU], x0[kU], g0[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      x1[u] = xn[i + u * st];
+      g1[u] = gn[i + u * st];
+      x0[u] = xp[i + u * st];
+      g0[u] = gp[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const T s = x1[u] - x0[u], y = g1[u] - g0[u];
+      sv[i + u * st] = s;
+      yv[i + u * st] = y;
+      xp[i + u * st] = x1[u];
+      gp[i + u * st] = g1[u];
+      a.add(s, y);
+      b.add(s, s);
+      c.add(y, y);
+    }
+  }
+  for (; i < n; i += st) {
     const T s = xn[i] - xp[i];
     const T y = gn[i] - gp[i];
     sv[i] = s;
     yv[i] = y;
     xp[i] = xn[i];
     gp[i] = gn[i];
-    a += (double)s * (double)y;
-    b += (double)s * (double)s;
-    c += (double)y * (double)y;
+    a.add(s, y);
+    b.add(s, s);
+    c.add(y, y);
   }
-  pw::block_sum_store(a, partial);
+  pw::block_sum_store(a.value(), partial);
   __syncthreads();
-  pw::block_sum_store(b, partial + kRedBlocks);
+  pw::block_sum_store(b.value(), partial + kRedBlocks);
   __syncthreads();
-  pw::block_sum_store(c, partial + 2 * kRedBlocks);
+  pw::block_sum_store(c.value(), partial + 2 * kRedBlocks);
 }
 
 template <typename T> __global__ void k_dot(const T *__restrict__ a, const T *__restrict__ b, int64_t n, double *partial) {
-  double acc = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += (double)a[i] * (double)b[i];
-  pw::block_sum_store(acc, partial);
+  pw::DotAcc<T> acc;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kU - 1) * st < n; i += kU * st) {
+    T av[kU], bv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      av[u] = a[i + u * st];
+      bv[u] = b[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) acc.add(av[u], bv[u]);
+  }
+  for (; i < n; i += st) acc.add(a[i], b[i]);
+  pw::block_sum_store(acc.value(), partial);
 }
 
 // coefficient on the device: c = c0 * (*p1) + c1 * (*p2) (pointers may be null)
@@ -58,14 +100,31 @@ struct Coef {
 template <typename T>
 __global__ void k_axpy_dot(T *v, const T *__restrict__ x, Coef cf, int64_t n, const T *__restrict__ dotv,
                            double *partial) {
-  const double c = cf.eval();
-  double acc = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T nv = v[i] + (T)c * x[i];
-    v[i] = nv;
-    if (dotv) acc += (double)dotv[i] * (double)nv;
+  const T c = (T)cf.eval();
+  pw::DotAcc<T> acc;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kU - 1) * st < n; i += kU * st) {
+    T vv[kU], xv[kU], dv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      vv[u] = v[i + u * st];
+      xv[u] = x[i + u * st];
+      dv[u] = dotv ? dotv[i + u * st] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const T nv = vv[u] + c * xv[u];
+      v[i + u * st] = nv;
+      if (dotv) acc.add(dv[u], nv);
+    }
   }
-  if (dotv) pw::block_sum_store(acc, partial);
+  for (; i < n; i += st) {
+    const T nv = v[i] + c * x[i];
+    v[i] = nv;
+    if (dotv) acc.add(dotv[i], nv);
+  }
+  if (dotv) pw::block_sum_store(acc.value(), partial);
 }
 
 template <typename T> __global__ void k_scale_copy(const T *__restrict__ x, double a, T *__restrict__ out, int64_t n) {
@@ -182,16 +241,23 @@ pm_status step_impl(lbfgs_state *s, const T *xn, const T *gn, T *d, double *gdot
     ::pm::note_launch();
     k_scale_copy<T><<<nb, nt, 0, st>>>(d, gam, d, n);
   }
-  for (int a = k - 1; a >= 0; --a) {  // oldest -> newest
-    const int i = idx(a);
+  if (k > 0) {  // y_oldest . r
     ::pm::note_launch();
-    k_dot<T><<<nb, nt, 0, st>>>(static_cast<const T *>(vec<T>(s, s->Y, i)), d, n, s->partial);
+    k_dot<T><<<nb, nt, 0, st>>>(static_cast<const T *>(vec<T>(s, s->Y, idx(k - 1))), d, n, s->partial);
     ::pm::note_launch();
     pm::pw::k_sum_partials<<<1, nt, 0, st>>>(s->partial, nb, dots + 4);
-    // r += (alpha_i - rho_i y_i.r) s_i
+  }
+  for (int a = k - 1; a >= 0; --a) {  // oldest -> newest
+    const int i = idx(a);
+    // r += (alpha_i - rho_i y_i.r) s_i, fused with y_next . r of the next pair
+    const T *next_y = a > 0 ? static_cast<const T *>(vec<T>(s, s->Y, idx(a - 1))) : nullptr;
     Coef cf{1.0, -s->rho[i], alpha + i, dots + 4};
     ::pm::note_launch();
-    k_axpy_dot<T><<<nb, nt, 0, st>>>(d, static_cast<const T *>(vec<T>(s, s->S, i)), cf, n, nullptr, nullptr);
+    k_axpy_dot<T><<<nb, nt, 0, st>>>(d, static_cast<const T *>(vec<T>(s, s->S, i)), cf, n, next_y, s->partial);
+    if (next_y) {
+      ::pm::note_launch();
+      pm::pw::k_sum_partials<<<1, nt, 0, st>>>(s->partial, nb, dots + 4);
+    }
   }
   // d = -r
   ::pm::note_launch();
