@@ -54,6 +54,24 @@ template <> struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Per-thread sum with the same scheme: FP64 for FP64 data; for FP32 data a
+// TwoSum-compensated FP32 pair, converted to FP64 once per thread.
+template <typename T> struct SumAcc {
+  double acc = 0.0;
+  __device__ __forceinline__ void add(T x) { acc += (double)x; }
+  __device__ __forceinline__ double value() const { return acc; }
+};
+template <> struct SumAcc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // out[slot] = sum of partial[0..n) in a fixed order (one block).
 static __global__ void k_sum_partials(const double *__restrict__ partial, int n, double *out) {
   __shared__ double sh[kRedThreads];
@@ -70,12 +88,12 @@ static __global__ void k_sum_partials(const double *__restrict__ partial, int n,
 
 // sum x^2 (prior), block partials
 template <typename T> __global__ void k_sumsq(const T *__restrict__ x, int64_t n, double *partial) {
-  double acc = 0.0;
+  DotAcc<T> acc;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)x[i];
-    acc += v * v;
+    const T v = x[i];
+    acc.add(v, v);
   }
-  block_sum_store(acc, partial);
+  block_sum_store(acc.value(), partial);
 }
 
 // IC amplitude on the half spectrum: sqrt(P(|k|) / Delta^3), P from the
@@ -130,7 +148,7 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
                        const T *__restrict__ data, const T *__restrict__ resp, const T *__restrict__ cot,
                        T *__restrict__ dbar, T *__restrict__ delta_out, int64_t n, double *partial) {
   const int e = -__ldg(fx_exp);
-  double acc = 0.0;
+  SumAcc<T> acc;  // the likelihood terms, each formed in T
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T delta;
     if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i]), e) - 1.0f;
@@ -140,7 +158,7 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
     T g = T(0);
     if (lp.lik == 0) {
       const T res = (T)lp.b * delta - data[i];
-      acc += 0.5 * (double)r * (double)res * (double)res * lp.inv_s2;
+      acc.add(T(0.5) * r * res * res * (T)lp.inv_s2);
       g = r * (T)lp.b * res * (T)lp.inv_s2;
     } else if (r > T(0)) {
       const T onep = T(1) + delta;
@@ -149,14 +167,14 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
       const T pw = pow(base, (T)lp.alpha);
       const T lam = r * (T)lp.nbar * pw * sg;
       const T cnt = data[i];
-      acc += (double)lam - (double)cnt * (double)log(lam);
+      acc.add(lam - cnt * log(lam));
       const T dpow = onep > (T)lp.rho_floor ? (T)lp.alpha * pw / base : T(0);
       const T dg = dpow * sg + pw * (T)lp.K * sg * (T(1) - sg);
       g = r * (T)lp.nbar * dg * (T(1) - cnt / lam);
     }
     if (dbar) dbar[i] = (T)lp.lw * g + (cot ? cot[i] : T(0));
   }
-  block_sum_store(acc, partial);
+  block_sum_store(acc.value(), partial);
 }
 
 // Model mean per cell from the fixed-point density (mock generation).

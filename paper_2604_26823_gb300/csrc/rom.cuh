@@ -35,16 +35,25 @@ __device__ __forceinline__ double counter_normal(unsigned long long key, unsigne
   return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
 
-// FP64 sum and sum of squared deviations (mean from results[slot_mu] when given)
+// Block partials of the sum, or (mean from results[slot_mu] given) of the
+// sum of squared deviations; FP64 partials.
 template <typename T>
 __global__ void k_moment(const T *__restrict__ x, int64_t n, const double *mean_sum, double *partial) {
-  const double mu = mean_sum ? *mean_sum / (double)n : 0.0;
-  double acc = 0.0;
+  // FP32 data: the deviation is formed in FP32 from the rounded mean (its
+  // rounding is ~1e-7 of the deviation, far inside the FP32 path's 1e-6
+  // projection tolerance) and both sums are compensated (pw::DotAcc/SumAcc)
+  const T mu = mean_sum ? (T)(*mean_sum / (double)n) : T(0);
+  pw::SumAcc<T> s1;
+  pw::DotAcc<T> s2;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)x[i] - mu;
-    acc += mean_sum ? v * v : (double)x[i];
+    if (mean_sum) {
+      const T v = x[i] - mu;
+      s2.add(v, v);
+    } else {
+      s1.add(x[i]);
+    }
   }
-  pw::block_sum_store(acc, partial);
+  pw::block_sum_store(mean_sum ? s2.value() : s1.value(), partial);
 }
 
 // Projection scalars once: mu, sd and 1/sd (FP64) from the two FP64 sums.
