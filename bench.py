@@ -37,10 +37,11 @@ N, BOX, STEPS_PM = 256, 500.0, 10
 NBAR = 1e-3
 ROM_EVERY = 20
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the launches of one gradient evaluation of this workload) from one ncu
-# capture of the kernel as it stands; profiles/deposit_traffic_masked_recon_256.md
-# gives the command.  Set to None when the kernel changes.
-NCU_TRAFFIC = {"adj_paint": 1084.2e6}
+# over the cotangent-paint launches of one gradient evaluation of this
+# workload, k = 9 .. 0) from one ncu capture of the kernel as it stands;
+# profiles/deposit_traffic_masked_recon_256.md gives the command.  Set to None
+# when the kernel changes.
+NCU_TRAFFIC = {"adj_paint": 1152.3e6}
 
 def config(api, nbar_cell, precision="f32"):
     from paper_2604_26823_gb300 import recon

@@ -617,6 +617,18 @@ template <typename T> struct Engine {
   pm_status reverse_step(int k, const T *xk, const V4<T> *phik) {
     const part::Geo g = geo();
     const int nb = grid_for(M, 256);
+    if (k == cfg.n_steps && cfg.rsd_axis < 0) {
+      // Without a redshift-space shift the final state's momentum cotangent is
+      // exactly zero, so the last kick's adjoint (cotangent paint, adjoint
+      // force, gather) adds exact zeros: only the reverse drift remains.
+      PM_CUDA_TRY(cudaMemsetAsync(maxslot, 0, sizeof(unsigned long long), st));
+      const T drift = k > 0 ? (T)dr[k - 1] : T(0);
+      const T cnext = k > 0 ? (T)ck[k - 1] : T(0);
+      ::pm::note_launch();
+      part::k_reverse_drift<T><<<nb, 256, 0, st>>>(g, xbar, pbar, drift, cnext, k > 0 ? maxslot : nullptr);
+      PM_LAUNCH_CHECK();
+      return PM_OK;
+    }
     PM_TRY(memset_fx(3));
     {
       ProfScope ps(prof, P_ADJ_PAINT, st, (double)M * (6 * sizeof(T) + 24));

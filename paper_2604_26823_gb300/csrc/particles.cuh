@@ -443,6 +443,31 @@ __global__ void k_adj_gather(Geo g, const T *__restrict__ x, const V4<T> *__rest
   }
 }
 
+// Reverse drift alone (a reverse step whose kick cotangent is zero):
+// pbar += drift * xbar, then the running max of |cnext pbar|; the same
+// arithmetic as k_adj_gather with a zero gather.
+template <typename T>
+__global__ void k_reverse_drift(Geo g, const T *__restrict__ xbar, T *__restrict__ pbar, T drift, T cnext,
+                                unsigned long long *maxslot) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T mx = T(0);
+  if (p < g.np) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T pb = pbar[a * g.np + p];
+      if (drift != T(0)) {
+        pb += drift * xbar[a * g.np + p];
+        pbar[a * g.np + p] = pb;
+      }
+      mx = max(mx, fabs(cnext * pb));
+    }
+  }
+  if (maxslot) {
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_abs<T>(maxslot, mx);
+  }
+}
+
 // 2LPT adjoint, per particle (= per Lagrangian node): psi1bar, psi2bar.
 template <typename T>
 __global__ void k_lpt_adj(int64_t np, const T *__restrict__ xbar, const T *__restrict__ pbar, T d1, T d2,
