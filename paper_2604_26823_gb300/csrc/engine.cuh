@@ -24,17 +24,23 @@ template <typename T> struct FftCfg {
 };
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
-template <typename T, int N> struct ZCfg {
-  static constexpr int B = FftCfg<T>::B;
+// z-pass tiles.  SMALL (used by the c2r pass): FP32 meshes up to 256^3 take
+// tiles of 8 rows on 128 threads (up to six CTAs per SM; measured 5% faster
+// for the 3-input c2r at 256^3).  Otherwise, and for the r2c pass (whose
+// fixed-point loader measured faster on the wide tile), FftCfg rows on 256
+// (512 at N = 512) threads.
+template <typename T, int N, bool SMALL = false> struct ZCfg {
+  static constexpr bool kSmall = SMALL && sizeof(T) == 4 && N <= 256;
+  static constexpr int B = kSmall ? 8 : FftCfg<T>::B;
   static constexpr int LEN = N / 2;
-  static constexpr int NT = cmin(N == 512 ? 512 : 256, B * LEN);
+  static constexpr int NT = kSmall ? cmin(128, B * LEN) : cmin(N == 512 ? 512 : 256, B * LEN);
   static constexpr size_t SMEM = (size_t)LEN * (B + 1) * sizeof(cx<T>);
-  // FP32, 256-thread tiles: CTAs per SM the c2r pass with NIN inputs can
-  // hold by shared memory (up to 3); its register budget is capped to match,
-  // so registers do not set a lower occupancy than shared memory does.  The
-  // FP64 and 512-thread variants keep the full budget (they would spill).
+  // CTAs per SM the c2r pass with NIN inputs can hold by shared memory (up
+  // to 6); its register budget is capped to match, so registers do not set a
+  // lower occupancy than shared memory does.  The FP64 and N = 512 variants
+  // keep the full budget (they would spill).
   template <int NIN> static constexpr int minb() {
-    return (sizeof(T) == 4 && NT <= 256) ? cmax(1, cmin(3, (int)((227u * 1024u) / (NIN * SMEM)))) : 1;
+    return kSmall ? cmax(1, cmin(6, (int)((227u * 1024u) / (NIN * SMEM)))) : 1;
   }
 };
 template <typename T, int N> struct CCfg {
@@ -380,7 +386,7 @@ template <typename T> struct Engine {
     for (int i = 0; i < NIN; ++i) ins.p[i] = slot(first_slot + i);
     ProfScope ps(prof, P_Z_C2R, st, (double)nb * NIN * S * sizeof(C) + (double)nb * M * Out::kWriteBytes);
     PM_DISPATCH_N(n, {
-      using Z = ZCfg<T, NN>;
+      using Z = ZCfg<T, NN, true>;
       auto kern = fft::k_z_c2r<T, NN, Z::B, Z::NT, NIN, Out, Z::template minb<NIN>()>;
       set_smem(kern, NIN * Z::SMEM);
       ::pm::note_launch();
