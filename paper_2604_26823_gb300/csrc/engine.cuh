@@ -200,6 +200,7 @@ template <typename T> struct Engine {
   double *partial = nullptr, *results = nullptr;
   int *fx_exp = nullptr;
   unsigned long long *maxslot = nullptr;
+  unsigned long long *maxslots = nullptr;  // part::kMaxSlots partial maxima (zero between uses)
   void *sort_ws = nullptr;
   Profiler prof;
 
@@ -251,6 +252,7 @@ template <typename T> struct Engine {
     results = partial + pw::kRedBlocks;
     fx_exp = reinterpret_cast<int *>(results + 16);
     maxslot = reinterpret_cast<unsigned long long *>(fx_exp + 8);
+    maxslots = maxslot + 8;
 
     // coefficients (host FP64)
     const pmhost::Schedule sch = pmhost::leapfrog(c.omega_m, c.a_init, c.n_steps);
@@ -278,6 +280,7 @@ template <typename T> struct Engine {
       h_tw[m] = mkc<C>((T)std::cos(ang), (T)std::sin(ang));
     }
     PM_CUDA_TRY(cudaMemcpy(tw, h_tw.data(), n * sizeof(C), cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemset(maxslots, 0, part::kMaxSlots * sizeof(unsigned long long)));
     // IC amplitude (table staged in the spectrum buffer)
     if ((size_t)npk * 16 > (size_t)S * sizeof(C)) {
       set_error("power table too large for this mesh");
@@ -421,6 +424,13 @@ template <typename T> struct Engine {
   pm_status set_exp(int slot_i, int v) {
     ::pm::note_launch();
     k_set_int<<<1, 1, 0, st>>>(fx_exp + slot_i, v);
+    PM_LAUNCH_CHECK();
+    return PM_OK;
+  }
+  // maxslot = max of the partial maxima a running-max kernel left in maxslots
+  pm_status fold_max() {
+    ::pm::note_launch();
+    part::k_fold_max<T><<<1, part::kMaxSlots, 0, st>>>(maxslots, maxslot);
     PM_LAUNCH_CHECK();
     return PM_OK;
   }
@@ -627,13 +637,12 @@ template <typename T> struct Engine {
       // Without a redshift-space shift the final state's momentum cotangent is
       // exactly zero, so the last kick's adjoint (cotangent paint, adjoint
       // force, gather) adds exact zeros: only the reverse drift remains.
-      PM_CUDA_TRY(cudaMemsetAsync(maxslot, 0, sizeof(unsigned long long), st));
       const T drift = k > 0 ? (T)dr[k - 1] : T(0);
       const T cnext = k > 0 ? (T)ck[k - 1] : T(0);
       ::pm::note_launch();
-      part::k_reverse_drift<T><<<nb, 256, 0, st>>>(g, xbar, pbar, drift, cnext, k > 0 ? maxslot : nullptr);
+      part::k_reverse_drift<T><<<nb, 256, 0, st>>>(g, xbar, pbar, drift, cnext, k > 0 ? maxslots : nullptr);
       PM_LAUNCH_CHECK();
-      return PM_OK;
+      return k > 0 ? fold_max() : PM_OK;
     }
     PM_TRY(memset_fx(3));
     {
@@ -641,17 +650,16 @@ template <typename T> struct Engine {
       PM_TRY(deposit(part::SrcAdj3<T>{g.L, M, g.log2np, xk, pbar, (T)ck[k], maxslot, fx_exp + 1, 0}));
     }
     PM_TRY(adjoint_force(src));
-    PM_CUDA_TRY(cudaMemsetAsync(maxslot, 0, sizeof(unsigned long long), st));
     const T drift = k > 0 ? (T)dr[k - 1] : T(0);
     const T cnext = k > 0 ? (T)ck[k - 1] : T(0);
     {
       ProfScope ps(prof, P_ADJ_GATHER, st, (double)M * 20 * sizeof(T));
       ::pm::note_launch();
       part::k_adj_gather<T><<<nb, 256, 0, st>>>(g, xk, phik, src, (T)ck[k], xbar, pbar, drift, cnext,
-                                                 k > 0 ? maxslot : nullptr);
+                                                 k > 0 ? maxslots : nullptr);
     }
     PM_LAUNCH_CHECK();
-    return PM_OK;
+    return k > 0 ? fold_max() : PM_OK;
   }
 
   pm_status adjoint(const T *s, const T *data, const T *R, double lw, const T *cot, double *loss_out,
@@ -663,10 +671,10 @@ template <typename T> struct Engine {
     const int nb = grid_for(M, 256);
     // final paint + RSD
     const T *xn = keep_all() ? dstate(ns) : dwork;
-    PM_CUDA_TRY(cudaMemsetAsync(maxslot, 0, sizeof(unsigned long long), st));
     ::pm::note_launch();
-    part::k_adj_final<T><<<nb, 256, 0, st>>>(g, xn, mom, cfg.rsd_axis, (T)rsd, dbar, xbar, pbar, (T)ck[ns], maxslot);
+    part::k_adj_final<T><<<nb, 256, 0, st>>>(g, xn, mom, cfg.rsd_axis, (T)rsd, dbar, xbar, pbar, (T)ck[ns], maxslots);
     PM_LAUNCH_CHECK();
+    PM_TRY(fold_max());
     if (keep_all()) {
       for (int k = ns; k >= 0; --k) PM_TRY(reverse_step(k, dstate(k), pstate(k)));
     } else {

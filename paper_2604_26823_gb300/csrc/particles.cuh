@@ -142,6 +142,43 @@ template <typename T> __device__ __forceinline__ T read_max_abs(const unsigned l
   else return __longlong_as_double((long long)*slot);
 }
 
+// Running max of |v| over a launch.  One atomic per warp on a single word
+// serialises at the L2 (524k same-address atomics at 256^3 cost ~0.25 ms), so
+// each block reduces to one value, which goes to one of kMaxSlots words
+// (chosen by block index, so the atomics spread over the L2); k_fold_max then
+// folds the words into the single slot the next paint reads.  Every thread of
+// the block must call this (it synchronises the block).
+constexpr int kMaxSlots = 256;
+template <typename T> __device__ __forceinline__ void block_max_to_slots(T mx, unsigned long long *slots) {
+  __shared__ T wmax[32];
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) wmax[w] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T m = wmax[0];
+    for (int i = 1; i < nw; ++i) m = max(m, wmax[i]);
+    atomic_max_abs<T>(slots + (blockIdx.x & (kMaxSlots - 1)), m);
+  }
+}
+
+// maxslot = max over the kMaxSlots words; the words are cleared for the next
+// launch.  One block of kMaxSlots threads.
+template <typename T> __global__ void k_fold_max(unsigned long long *slots, unsigned long long *maxslot) {
+  __shared__ T sh[kMaxSlots];
+  sh[threadIdx.x] = read_max_abs<T>(slots + threadIdx.x);
+  slots[threadIdx.x] = 0ull;
+  __syncthreads();
+  for (int st = kMaxSlots / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] = max(sh[threadIdx.x], sh[threadIdx.x + st]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *maxslot = 0ull;
+    atomic_max_abs<T>(maxslot, sh[0]);
+  }
+}
+
 // Exponent E with 2^E * maxabs * n_particles < 2^61 (no overflow of the
 // int64 accumulators); deposits are rint(w * 2^E).
 __device__ __forceinline__ int fixed_exponent(double maxabs, int log2_particles) {
@@ -408,9 +445,7 @@ __global__ void k_adj_final(Geo g, const T *__restrict__ x, const T *__restrict_
       mx = max(mx, fabs(cn * pb[a]));
     }
   }
-  // warp max then one atomic per warp
-  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_abs<T>(maxslot, mx);
+  block_max_to_slots<T>(mx, maxslot);
 }
 
 // Adjoint gather at x_k: xbar += grad_u sum W (c_k pbar . Phi_k + rhobar);
@@ -437,10 +472,7 @@ __global__ void k_adj_gather(Geo g, const T *__restrict__ x, const V4<T> *__rest
       mx = max(mx, fabs(cnext * pb[a]));
     }
   }
-  if (maxslot) {
-    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_abs<T>(maxslot, mx);
-  }
+  if (maxslot) block_max_to_slots<T>(mx, maxslot);
 }
 
 // Reverse drift alone (a reverse step whose kick cotangent is zero):
@@ -462,10 +494,7 @@ __global__ void k_reverse_drift(Geo g, const T *__restrict__ xbar, T *__restrict
       mx = max(mx, fabs(cnext * pb));
     }
   }
-  if (maxslot) {
-    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_abs<T>(maxslot, mx);
-  }
+  if (maxslot) block_max_to_slots<T>(mx, maxslot);
 }
 
 // 2LPT adjoint, per particle (= per Lagrangian node): psi1bar, psi2bar.
