@@ -87,16 +87,29 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup():
+def dist_setup(backend=None):
+    """Rank / world size from the launcher's environment; with several ranks,
+    a process group (NCCL on GPUs; gloo when given or without CUDA)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return ws, rank, local
+
+
+def replica_seeds(rank):
+    """Seeds of one replica: each rank reconstructs its own mock (replicas
+    only; no data-path collective)."""
+    return {"truth": 1 + 1000 * rank, "counts": 3 + 1000 * rank, "start": 2 + 1000 * rank}
 
 
 def max_over_ranks(x, ws):
@@ -104,9 +117,15 @@ def max_over_ranks(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds_local):
+    """Units all ranks processed / the slowest rank's time (max over ranks)."""
+    return ws * units_per_rank / max_over_ranks(seconds_local, ws)
 
 
 def barrier(ws):
@@ -208,8 +227,9 @@ def run_ours(args, ws, rank, local):
     lnk, lnp = api.pm_linear_power_table()
     dev = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
 
+    seeds = replica_seeds(rank)
     R_h, s_true, counts_h, nbar_cell = recon.masked_mock(N, BOX, n_steps=STEPS_PM, nbar=NBAR,
-                                                         seed_truth=1 + 1000 * rank, seed_counts=3 + 1000 * rank,
+                                                         seed_truth=seeds["truth"], seed_counts=seeds["counts"],
                                                          lnk=lnk, lnp=lnp)
     cfg = config(api, nbar_cell)
     plan = api.Plan(cfg, lnk, lnp)
@@ -221,7 +241,7 @@ def run_ours(args, ws, rank, local):
     t_real = dev(inputs.sorted_normal_targets(ncount, 7))
     t_four = dev(inputs.sorted_normal_targets_per_bin(api.pm_rom_fourier_counts(plan), 8))
     st = api.LBFGS(N ** 3, m=10, precision="f32")
-    s0 = inputs.white_noise(N, 2 + 1000 * rank)
+    s0 = inputs.white_noise(N, seeds["start"])
     state = {"s": dev(s0), "g": torch.empty((N, N, N), dtype=torch.float32, device="cuda"),
              "trial": torch.empty((N, N, N), dtype=torch.float32, device="cuda"), "it": 0}
     _, state["g"] = api.pm_adjoint(plan, state["s"], counts, R, grad_out=state["g"])
@@ -264,8 +284,8 @@ def run_ours(args, ws, rank, local):
     prof = {c: api.pm_profile_read(plan, c) for c in api.PROFILE_CLASSES}
     api.pm_profile(plan, False)
     barrier(ws)
-    ms_max = max_over_ranks(ms, ws)
-    value = ws * args.steps / (ms_max / 1e3)
+    value = whole_job_rate(args.steps, ws, ms / 1e3)
+    ms_max = ws * args.steps / value * 1e3
 
     # dominant kernel class: algorithmic bytes (recorded per launch by the
     # library) over its event-timed duration, against the measured HBM peak
