@@ -54,7 +54,9 @@ typedef struct {
   int32_t n;                /* mesh cells per side = particles per side; power of two, 16..512 */
   int32_t n_steps;          /* leapfrog steps, uniform in a from a_init to 1 (Sec. 2.2.1 item 2); >= 1 */
   int32_t lpt_order;        /* 1 (Zel'dovich) or 2 (2LPT, the paper's choice) */
-  int32_t rsd_axis;         /* -1: no redshift-space shift; 0, 1, 2: plane-parallel shift along x, y, z */
+  int32_t rsd_axis;         /* redshift-space shift at a = 1 (Sec. 2.2.1 item 3): -1 none; 0, 1, 2:
+                               plane parallel along x, y, z; 3: radial, along the line of sight from
+                               `observer` (x_s = x + (p . d) d / (a^2 E), d the unit vector) */
   int32_t likelihood;       /* PM_LIK_GAUSSIAN: linear bias b, 1/2 sum R (b delta - d)^2 / sigma^2
                                PM_LIK_POISSON: Eq. galaxy_bias with R and the Poisson likelihood of Sec. 2.2.2 */
   int32_t precision;        /* PM_PREC_F32 (FP32 mesh / FFT / particles, FP64 reductions) or PM_PREC_F64 */
@@ -72,6 +74,8 @@ typedef struct {
   double nbar_cell;         /* Poisson: normalisation N_G of Eq. galaxy_bias, galaxies per cell */
   double rho_floor;         /* Poisson: floor on 1 + delta inside the power law (1e-3) */
   double prior_weight;      /* weight w of the Gaussian prior (w/2) sum s^2; 0 = likelihood only */
+  double observer[3];       /* rsd_axis = 3: observer position in box coordinates, Mpc/h (may lie
+                               outside the box; no particle may sit on it) */
 } pm_config;
 
 typedef struct pm_plan pm_plan;

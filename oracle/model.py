@@ -37,7 +37,8 @@ class Config:
     a_init: float = 0.1
     n_steps: int = 5
     lpt_order: int = 2
-    rsd_axis: int = -1          # -1: none, 0..2: plane-parallel shift along that axis
+    rsd_axis: int = -1          # -1: none, 0..2: plane-parallel shift along that axis, 3: radial
+    observer: tuple = (0.0, 0.0, 0.0)   # Mpc/h, box coordinates (radial shift only)
     likelihood: str = "gaussian"   # "gaussian" (linear bias) | "poisson" (power law + sigmoid)
     bias_b: float = 1.5
     sigma: float = 1.0
@@ -183,12 +184,46 @@ def rsd_coefficient(cfg):
     return 1.0 / (a * a * float(cosmo.efunc(a, cfg.omega_m)))
 
 
+def _line_of_sight(disp, cfg):
+    """Unit vectors d = r/|r| from the observer to each particle, r = q + disp - o
+    (unwrapped comoving position, Mpc/h), and |r|."""
+    r = M.lattice_cells(cfg.n) * cfg.cell + disp - np.asarray(cfg.observer, np.float64)
+    rn = np.sqrt(np.sum(r * r, axis=1))
+    return r / rn[:, None], rn
+
+
 def observed_positions(disp, mom, cfg):
-    """Displacement after the plane-parallel RSD shift."""
+    """Displacement after the RSD shift (Sec. 2.2.1 item 3): along a fixed box
+    axis (plane parallel), or along the line of sight from the observer,
+    x_s = x + c (p . d) d with d the unit vector from the observer (radial)."""
     out = disp.copy()
-    if cfg.rsd_axis >= 0:
+    if 0 <= cfg.rsd_axis <= 2:
         out[:, cfg.rsd_axis] += rsd_coefficient(cfg) * mom[:, cfg.rsd_axis]
+    elif cfg.rsd_axis == 3:
+        d, _ = _line_of_sight(disp, cfg)
+        out += rsd_coefficient(cfg) * np.sum(mom * d, axis=1)[:, None] * d
     return out
+
+
+def observed_positions_vjp(disp, mom, xsbar, cfg):
+    """Transpose of the Jacobian of observed_positions applied to the cotangent
+    xsbar of the shifted positions: returns (xbar, pbar).  Radial case, with
+    P = I - d d^T and dd/dx = P/|r|:
+      pbar = c d (d . xsbar),
+      xbar = xsbar + (c/|r|) [P p (d . xsbar) + (p . d) P xsbar]."""
+    c = rsd_coefficient(cfg)
+    xbar = xsbar.copy()
+    pbar = np.zeros_like(xsbar)
+    if 0 <= cfg.rsd_axis <= 2:
+        pbar[:, cfg.rsd_axis] = c * xsbar[:, cfg.rsd_axis]
+    elif cfg.rsd_axis == 3:
+        d, rn = _line_of_sight(disp, cfg)
+        dxs = np.sum(d * xsbar, axis=1)[:, None]
+        pd = np.sum(mom * d, axis=1)[:, None]
+        proj = lambda v: v - d * np.sum(d * v, axis=1)[:, None]
+        pbar = c * d * dxs
+        xbar = xsbar + (c / rn)[:, None] * (proj(mom) * dxs + pd * proj(xsbar))
+    return xbar, pbar
 
 
 def final_density(disp_obs, cfg):
@@ -255,10 +290,8 @@ def gradient(s, cfg, lnk, lnp, data, resp, loss_weight=1.0, cot_delta=None):
     if cot_delta is not None:
         dbar = dbar + cot_delta
     # final paint: delta = paint(u_obs) - 1
-    xbar = M.cic_readout_grad(positions_cells(obs, cfg), dbar) / cfg.cell
-    pbar = np.zeros_like(xbar)
-    if cfg.rsd_axis >= 0:
-        pbar[:, cfg.rsd_axis] += rsd_coefficient(cfg) * xbar[:, cfg.rsd_axis]
+    xsbar = M.cic_readout_grad(positions_cells(obs, cfg), dbar) / cfg.cell
+    xbar, pbar = observed_positions_vjp(disp, mom, xsbar, cfg)
     # leapfrog steps in reverse
     for k in range(cfg.n_steps - 1, -1, -1):
         xbar = xbar + force_vjp(disp_k[k + 1], sch["Kb"][k] * pbar, cfg, ops)

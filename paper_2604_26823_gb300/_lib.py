@@ -32,7 +32,7 @@ class pm_config(ctypes.Structure):
         ("box", ctypes.c_double), ("omega_m", ctypes.c_double), ("a_init", ctypes.c_double),
         ("bias_b", ctypes.c_double), ("sigma", ctypes.c_double), ("alpha", ctypes.c_double),
         ("delta_th", ctypes.c_double), ("K", ctypes.c_double), ("nbar_cell", ctypes.c_double),
-        ("rho_floor", ctypes.c_double), ("prior_weight", ctypes.c_double),
+        ("rho_floor", ctypes.c_double), ("prior_weight", ctypes.c_double), ("observer", ctypes.c_double * 3),
     ]
 
 

@@ -37,7 +37,7 @@ class Config:
     box: float
     n_steps: int = 10
     lpt_order: int = 2
-    rsd_axis: int = -1
+    rsd_axis: int = -1                # -1 none, 0..2 plane parallel, 3 radial from `observer`
     likelihood: str = "gaussian"      # "gaussian" | "poisson"
     precision: str = "f32"            # "f32" | "f64"
     checkpoint_every: int = 0
@@ -51,6 +51,7 @@ class Config:
     nbar_cell: float = 1.0
     rho_floor: float = 1e-3
     prior_weight: float = 1.0
+    observer: tuple = (0.0, 0.0, 0.0)  # Mpc/h, box coordinates (rsd_axis = 3)
 
     def to_c(self):
         c = L.pm_config()
@@ -61,6 +62,8 @@ class Config:
         for f in ("box", "omega_m", "a_init", "bias_b", "sigma", "alpha", "delta_th", "K",
                   "nbar_cell", "rho_floor", "prior_weight"):
             setattr(c, f, float(getattr(self, f)))
+        for i in range(3):
+            c.observer[i] = float(self.observer[i])
         return c
 
     @property

@@ -37,7 +37,7 @@ pm_status pm_validate_config(const pm_config *c) {
     return PM_ERR_UNSUPPORTED;
   }
   if (c->n_steps < 1 || c->n_steps > 1000 || (c->lpt_order != 1 && c->lpt_order != 2) || c->rsd_axis < -1 ||
-      c->rsd_axis > 2 || (c->likelihood != PM_LIK_GAUSSIAN && c->likelihood != PM_LIK_POISSON) ||
+      c->rsd_axis > 3 || (c->likelihood != PM_LIK_GAUSSIAN && c->likelihood != PM_LIK_POISSON) ||
       (c->precision != PM_PREC_F32 && c->precision != PM_PREC_F64) || c->checkpoint_every < 0) {
     pm::set_error("invalid enum / step count / checkpoint setting");
     return PM_ERR_INVALID_ARG;
@@ -45,6 +45,11 @@ pm_status pm_validate_config(const pm_config *c) {
   if (!(c->box > 0) || !(c->a_init > 0) || !(c->a_init < 1) || !(c->omega_m > 0) || !(c->omega_m <= 1) ||
       !std::isfinite(c->prior_weight)) {
     pm::set_error("invalid box / a_init / omega_m / prior_weight");
+    return PM_ERR_INVALID_ARG;
+  }
+  if (c->rsd_axis == 3 &&
+      !(std::isfinite(c->observer[0]) && std::isfinite(c->observer[1]) && std::isfinite(c->observer[2]))) {
+    pm::set_error("radial redshift-space shift needs a finite observer position");
     return PM_ERR_INVALID_ARG;
   }
   if (c->likelihood == PM_LIK_GAUSSIAN && !(c->sigma > 0)) {

@@ -204,6 +204,7 @@ template <typename T> struct Engine {
   void *sort_ws = nullptr;
   Profiler prof;
 
+  T obs_cell(int a) const { return (T)(cfg.observer[a] / cell); }  // observer in cell units
   part::Geo geo() const {
     part::Geo g;
     g.L.logn = logn;
@@ -560,7 +561,7 @@ template <typename T> struct Engine {
     const int fin = (keep && keep_all()) ? ns : 0;
     PM_TRY(memset_fx(1));
     return deposit(part::SrcFinal<T>{geo().L, M, pstate(fin), dstate(fin), mom, (T)ck[ns], cfg.rsd_axis, (T)rsd,
-                                         fx_exp, T(0)});
+                                     fx_exp, T(0), {obs_cell(0), obs_cell(1), obs_cell(2)}});
   }
 
   pm_status loss_terms(const T *s, const T *data, const T *R, const T *cot, double lw, bool want_dbar,
@@ -672,7 +673,8 @@ template <typename T> struct Engine {
     // final paint + RSD
     const T *xn = keep_all() ? dstate(ns) : dwork;
     ::pm::note_launch();
-    part::k_adj_final<T><<<nb, 256, 0, st>>>(g, xn, mom, cfg.rsd_axis, (T)rsd, dbar, xbar, pbar, (T)ck[ns], maxslots);
+    part::k_adj_final<T><<<nb, 256, 0, st>>>(g, xn, mom, cfg.rsd_axis, (T)rsd, obs_cell(0), obs_cell(1), obs_cell(2),
+                                              dbar, xbar, pbar, (T)ck[ns], maxslots);
     PM_LAUNCH_CHECK();
     PM_TRY(fold_max());
     if (keep_all()) {

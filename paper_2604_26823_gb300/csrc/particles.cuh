@@ -290,6 +290,40 @@ template <typename T> struct SrcKdk {
 
 // Last half kick p += kick F(x), then deposit x + rsd * p along rsd_axis
 // (fx_exp null: kick only).
+// Line of sight of particle p (radial redshift-space shift, Sec. 2.2.1 item
+// 3): r = node + d - o in cell units (the unwrapped position seen from the
+// observer o), unit vector u = r/|r| and 1/|r|.
+template <typename T>
+__device__ __forceinline__ void line_of_sight(const Lattice &L, int64_t p, const T (&d)[3], const T (&o)[3],
+                                              T (&u)[3], T &inv_r) {
+  int nd[3];
+  L.node(p, nd[0], nd[1], nd[2]);
+  T r[3], r2 = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r[a] = ((T)nd[a] + d[a]) - o[a];
+    r2 += r[a] * r[a];
+  }
+  inv_r = T(1) / sqrt(r2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = r[a] * inv_r;
+}
+
+// Shifted displacement along a box axis (0..2) or the line of sight (3).
+template <typename T>
+__device__ __forceinline__ void rsd_shift(const Lattice &L, int64_t p, int rsd_axis, T rsd, const T (&o)[3],
+                                          const T (&m)[3], T (&d)[3]) {
+  if (rsd_axis >= 0 && rsd_axis <= 2) {
+    d[rsd_axis] += rsd * m[rsd_axis];
+  } else if (rsd_axis == 3) {
+    T u[3], inv_r;
+    line_of_sight<T>(L, p, d, o, u, inv_r);
+    const T pu = m[0] * u[0] + m[1] * u[1] + m[2] * u[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] += rsd * pu * u[a];
+  }
+}
+
 template <typename T> struct SrcFinal {
   static constexpr int NCH = 1;
   Lattice L;
@@ -302,6 +336,7 @@ template <typename T> struct SrcFinal {
   T rsd;
   const int *fx_exp;
   T scale;
+  T obs[3];  // observer, cell units (rsd_axis = 3)
   __device__ void setup() { scale = fx_exp ? pow2<T>(__ldg(fx_exp)) : T(0); }
   __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
     T d[3] = {x[p], x[np + p], x[2 * np + p]};
@@ -314,7 +349,7 @@ template <typename T> struct SrcFinal {
       m[a] = mom[a * np + p] + kick * f[a];
       mom[a * np + p] = m[a];
     }
-    if (rsd_axis >= 0) d[rsd_axis] += rsd * m[rsd_axis];
+    rsd_shift<T>(L, p, rsd_axis, rsd, obs, m, d);
     c = locate<T>(L, p, d[0], d[1], d[2]);
     v[0] = scale;
     return fx_exp != nullptr;
@@ -425,22 +460,40 @@ __global__ void k_readout(Geo g, const V4<T> *__restrict__ phi, const T *__restr
 // pbar = rsd * xbar along the RSD axis; then the running max of |cn * pbar|.
 template <typename T>
 __global__ void k_adj_final(Geo g, const T *__restrict__ x, const T *__restrict__ mom, int rsd_axis, T rsd,
-                            const T *__restrict__ dbar, T *__restrict__ xbar, T *__restrict__ pbar, T cn,
-                            unsigned long long *maxslot) {
+                            T ox, T oy, T oz, const T *__restrict__ dbar, T *__restrict__ xbar,
+                            T *__restrict__ pbar, T cn, unsigned long long *maxslot) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   T mx = T(0);
   if (p < g.np) {
-    T d[3] = {x[p], x[g.np + p], x[2 * g.np + p]};
-    if (rsd_axis >= 0) d[rsd_axis] += rsd * mom[rsd_axis * g.np + p];
+    const T x0[3] = {x[p], x[g.np + p], x[2 * g.np + p]};
+    const T m[3] = {mom[p], mom[g.np + p], mom[2 * g.np + p]};
+    const T o[3] = {ox, oy, oz};
+    T d[3] = {x0[0], x0[1], x0[2]};
+    rsd_shift<T>(g.L, p, rsd_axis, rsd, o, m, d);
     const Cell<T> c = locate<T>(g.L, p, d[0], d[1], d[2]);
     T gx, gy, gz;
     grad_gather<T>(g.L, nullptr, dbar, c, T(0), T(0), T(0), gx, gy, gz);
     T pb[3] = {T(0), T(0), T(0)};
-    const T gg[3] = {gx, gy, gz};
-    if (rsd_axis >= 0) pb[rsd_axis] = rsd * gg[rsd_axis];
+    T xb[3] = {gx, gy, gz};
+    if (rsd_axis >= 0 && rsd_axis <= 2) {
+      pb[rsd_axis] = rsd * xb[rsd_axis];
+    } else if (rsd_axis == 3) {
+      // x_s = x + c (p.u) u:  pbar = c u (u.g),
+      // xbar = g + (c/|r|) [P p (u.g) + (p.u) P g],  P = I - u u^T
+      T u[3], inv_r;
+      line_of_sight<T>(g.L, p, x0, o, u, inv_r);
+      const T ug = u[0] * gx + u[1] * gy + u[2] * gz;
+      const T pu = m[0] * u[0] + m[1] * u[1] + m[2] * u[2];
+      const T gg[3] = {gx, gy, gz};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        pb[a] = rsd * u[a] * ug;
+        xb[a] = gg[a] + rsd * inv_r * ((m[a] - u[a] * pu) * ug + pu * (gg[a] - u[a] * ug));
+      }
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      xbar[a * g.np + p] = gg[a];
+      xbar[a * g.np + p] = xb[a];
       pbar[a * g.np + p] = pb[a];
       mx = max(mx, fabs(cn * pb[a]));
     }

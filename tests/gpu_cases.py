@@ -26,6 +26,11 @@ CASES = {
     # masked Poisson likelihood with the power-law + sigmoid bias, 64^3 in 125 Mpc/h
     "poisson64": dict(n=64, box=125.0, n_steps=4, lpt_order=2, rsd_axis=-1, likelihood="poisson",
                       nbar_cell=0.5, alpha=0.7, delta_th=1.2, K=3.0, rho_floor=1e-3, prior_weight=1.0),
+    # radial redshift-space shift seen from an observer outside the box (the
+    # paper's line of sight), masked Poisson likelihood, 64^3 in 125 Mpc/h
+    "radial64": dict(n=64, box=125.0, n_steps=4, lpt_order=2, rsd_axis=3, observer=(62.5, 62.5, -60.0),
+                     likelihood="poisson", nbar_cell=0.5, alpha=0.7, delta_th=1.2, K=3.0, rho_floor=1e-3,
+                     prior_weight=1.0),
     # Zel'dovich start, RSD along x, 16^3 (single-tile meshes)
     "tiny": dict(n=16, box=48.0, n_steps=3, lpt_order=1, rsd_axis=0, likelihood="gaussian",
                  bias_b=1.2, sigma=0.8, prior_weight=0.5),
@@ -33,7 +38,7 @@ CASES = {
 
 
 def oracle_config(kw):
-    keys = ("n", "box", "n_steps", "lpt_order", "rsd_axis", "likelihood", "bias_b", "sigma", "alpha",
+    keys = ("n", "box", "n_steps", "lpt_order", "rsd_axis", "observer", "likelihood", "bias_b", "sigma", "alpha",
             "delta_th", "K", "nbar_cell", "rho_floor", "prior_weight")
     return OM.Config(**{k: kw[k] for k in keys if k in kw})
 

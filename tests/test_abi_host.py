@@ -37,7 +37,7 @@ def test_exports_every_declared_symbol(lib):
 
 def test_config_struct_layout_matches_header(lib):
     from paper_2604_26823_gb300 import _lib
-    assert ctypes.sizeof(_lib.pm_config) == 8 * 4 + 11 * 8
+    assert ctypes.sizeof(_lib.pm_config) == 8 * 4 + 14 * 8
     assert lib.pm_version().decode().startswith("mujica-pm")
 
 

@@ -146,10 +146,13 @@ def _cases():
                      likelihood="gaussian", bias_b=1.5, sigma=1.0, prior_weight=1.0),
         model.Config(n=8, box=40.0, n_steps=2, lpt_order=2, rsd_axis=-1,
                      likelihood="poisson", nbar_cell=2.0, prior_weight=0.5),
+        # radial shift from an observer outside the box (the paper's line of sight)
+        model.Config(n=8, box=32.0, n_steps=2, lpt_order=2, rsd_axis=3, observer=(16.0, 20.0, -24.0),
+                     likelihood="gaussian", bias_b=1.5, sigma=1.0, prior_weight=1.0),
     ]
 
 
-@pytest.mark.parametrize("case", [0, 1])
+@pytest.mark.parametrize("case", [0, 1, 2])
 def test_gradient_brute_force_all_coordinates(table, case):
     """Central finite differences on every one of the 8^3 white-noise
     coordinates against the hand-derived adjoint."""
@@ -258,3 +261,46 @@ def test_rsd_kaiser_limit(table):
         assert abs(red[i] / real[i] - 1.0) < 1e-9
     # no momentum, no shift
     np.testing.assert_array_equal(model.observed_positions(disp, 0 * mom, cfg), disp)
+
+
+def test_radial_rsd_closed_forms():
+    """Radial shift: zero momentum leaves positions unchanged; for a distant
+    observer on the -z side it tends to the plane-parallel shift along z
+    (error ~ transverse distance / observer distance); the shift is along the
+    line of sight with length c (p . d)."""
+    n, box = 8, 32.0
+    rng = np.random.default_rng(5)
+    disp = rng.normal(0, 0.5, (n ** 3, 3))
+    mom = rng.normal(0, 1.0, (n ** 3, 3))
+    far = model.Config(n=n, box=box, rsd_axis=3, observer=(16.0, 16.0, -1e7))
+    pp = model.Config(n=n, box=box, rsd_axis=2)
+    np.testing.assert_array_equal(model.observed_positions(disp, 0 * mom, far), disp)
+    a, b = model.observed_positions(disp, mom, far), model.observed_positions(disp, mom, pp)
+    assert np.abs(a - b).max() < 1e-4 * np.abs(mom).max()
+    near = model.Config(n=n, box=box, rsd_axis=3, observer=(10.0, -5.0, -40.0))
+    shift = model.observed_positions(disp, mom, near) - disp
+    r = (np.array([[i, j, l] for i in range(n) for j in range(n) for l in range(n)], float) * (box / n)
+         + disp - np.array(near.observer))
+    d = r / np.linalg.norm(r, axis=1)[:, None]
+    c = model.rsd_coefficient(near)
+    np.testing.assert_allclose(shift, c * np.sum(mom * d, axis=1)[:, None] * d, rtol=1e-12, atol=1e-12)
+
+
+def test_radial_rsd_vjp_dot_product(table):
+    """<J v, w> = <v, J^T w> for the radial shift's Jacobian wrt (disp, mom),
+    by central differences along random directions."""
+    n, box = 8, 32.0
+    cfg = model.Config(n=n, box=box, rsd_axis=3, observer=(12.0, 40.0, -30.0))
+    rng = np.random.default_rng(6)
+    disp = rng.normal(0, 0.5, (n ** 3, 3))
+    mom = rng.normal(0, 1.0, (n ** 3, 3))
+    w = rng.standard_normal((n ** 3, 3))
+    xb, pb = model.observed_positions_vjp(disp, mom, w, cfg)
+    for _ in range(3):
+        vx, vp = rng.standard_normal((n ** 3, 3)), rng.standard_normal((n ** 3, 3))
+        h = 1e-6
+        jv = (model.observed_positions(disp + h * vx, mom + h * vp, cfg)
+              - model.observed_positions(disp - h * vx, mom - h * vp, cfg)) / (2 * h)
+        lhs = np.sum(jv * w)
+        rhs = np.sum(vx * xb) + np.sum(vp * pb)
+        assert abs(lhs - rhs) < 1e-7 * abs(rhs)
