@@ -297,6 +297,13 @@ def run_ours(args, ws, rank, local):
         pass
     classes = {k: {"ms_total": v[0], "launches": v[1], "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] else None}
                for k, v in prof.items()}
+    # byte model of the step: the algorithmic bytes the library records for its
+    # profiled kernel classes (inputs read once, outputs written once), per
+    # step, over the measured step time (end-to-end effective bandwidth)
+    alg_step = sum(v[2] for v in prof.values()) / args.steps
+    bytes_model = {"algorithmic_bytes_per_step": alg_step, "profiled_classes_ms_per_step":
+                   sum(v[0] for v in prof.values()) / args.steps,
+                   "effective_GBps": alg_step / (ms / args.steps / 1e3) / 1e9}
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_n, dom_b = prof[dom]
     roof = None
@@ -384,7 +391,7 @@ def run_ours(args, ws, rank, local):
                            "likelihood": "poisson", "galaxies": n_gal, "selection_volume_frac": vol_frac,
                            "parallelism": f"replicas x{ws}", "l2": "working set ~7 GB >> 129 MB L2 (no flush)"},
                 "fp64_path": fp64, "checkpointed_512": ck512, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-                "gpu_launches": int(launches), "clocks": clk, "kernel_classes": classes,
+                "gpu_launches": int(launches), "clocks": clk, "kernel_classes": classes, "bytes_model": bytes_model,
                 "final_loss": losses[-1]}
         print(json.dumps(line), flush=True)
 
