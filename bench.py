@@ -179,6 +179,30 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def fft_comparison(api, plan, s, reps=20):
+    import torch
+    out = torch.empty_like(s)
+    amp = torch.rand((N, N, N // 2 + 1), dtype=torch.float32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(f):
+        for _ in range(3):
+            f()
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ours = timed(lambda: api.pm_linear_field(plan, s, out=out))
+    cufft = timed(lambda: torch.fft.irfftn(torch.fft.rfftn(s) * amp, s=(N, N, N)))
+    return {"op": "linear field: real 256^3 -> spectrum x A(k) -> real (FP32)", "library_ms": ours,
+            "cufft_ms": cufft, "note": "comparison only; cuFFT is not used on the path"}
+
+
 def run_ckpt512(api, inputs, lnk, lnp, evals=3):
     """pm_adjoint at 512^3 in a 1000 Mpc/h box, 2LPT + 10 steps, Gaussian
     likelihood with b = 1.5 over the full box, particle states checkpointed
@@ -341,6 +365,13 @@ def run_ours(args, ws, rank, local):
 
     # checkpointed 512^3 configuration (1000 Mpc/h, 10 steps, states kept every
     # 2 steps): gradient evals/s and peak device memory
+    # cuFFT as a comparison only: the linear field delta_L = IFFT[A(k) FFT[s]]
+    # through the library's pencil passes (one r2c, y, fused x with the
+    # amplitude multiplier, y, c2r) against torch.fft (cuFFT) rfftn * A irfftn
+    # on the same 256^3 FP32 mesh (the cuFFT side skips the DC / Nyquist
+    # conventions, so only the times are compared)
+    fft_cmp = fft_comparison(api, plan, state["s"])
+
     ck512 = None
     if not args.no_512:
         del plan
@@ -390,7 +421,7 @@ def run_ours(args, ws, rank, local):
                            "pm_steps": STEPS_PM, "lbfgs_m": 10, "rom_every": ROM_EVERY,
                            "likelihood": "poisson", "galaxies": n_gal, "selection_volume_frac": vol_frac,
                            "parallelism": f"replicas x{ws}", "l2": "working set ~7 GB >> 129 MB L2 (no flush)"},
-                "fp64_path": fp64, "checkpointed_512": ck512, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+                "fp64_path": fp64, "checkpointed_512": ck512, "fft_vs_cufft": fft_cmp, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
                 "gpu_launches": int(launches), "clocks": clk, "kernel_classes": classes, "bytes_model": bytes_model,
                 "final_loss": losses[-1]}
         print(json.dumps(line), flush=True)
