@@ -204,3 +204,35 @@ def power_from_table(k, lnk_tab, lnp_tab):
     k = np.asarray(k, dtype=np.float64)
     safe = np.where(k > 0, k, 1.0)
     return np.where(k > 0, np.exp(np.interp(np.log(safe), lnk_tab, lnp_tab)), 0.0)
+
+
+C_OVER_H0 = 2997.92458  # speed of light / (100 km/s/Mpc), Mpc/h
+
+
+def comoving_distance(a, omega_m):
+    """chi(a) = (c/H0) int_a^1 da' / (a'^2 E(a')), Mpc/h, flat LCDM (adaptive
+    quadrature, one integral per value)."""
+    a = np.atleast_1d(np.asarray(a, dtype=np.float64))
+    f = lambda x: 1.0 / (x * x * float(efunc(x, omega_m)))
+    out = np.array([integrate.quad(f, ai, 1.0, epsabs=0.0, epsrel=1e-13, limit=200)[0] for ai in a])
+    return C_OVER_H0 * out
+
+
+def distance_table(omega_m, a_min=0.5, n=2049):
+    """(a_j, chi_j) on a uniform grid of a in [a_min, 1]: the table from which
+    the scale factor of a comoving distance is read (DistToScaleFactor of the
+    lightcone construction, Appendix A)."""
+    a = np.linspace(a_min, 1.0, n)
+    return a, comoving_distance(a, omega_m)
+
+
+def dist_to_scale_factor(d, a_tab, chi_tab):
+    """a(d) by linear interpolation of the table (chi decreases with a),
+    clamped to the table's ends; and da/dd of the interpolant (0 outside)."""
+    d = np.asarray(d, dtype=np.float64)
+    x, y = chi_tab[::-1], a_tab[::-1]          # increasing chi
+    a = np.interp(d, x, y)
+    j = np.clip(np.searchsorted(x, d, side="right") - 1, 0, len(x) - 2)
+    slope = (y[j + 1] - y[j]) / (x[j + 1] - x[j])
+    slope = np.where((d >= x[0]) & (d <= x[-1]), slope, 0.0)
+    return a, slope

@@ -38,7 +38,8 @@ class Config:
     n_steps: int = 5
     lpt_order: int = 2
     rsd_axis: int = -1          # -1: none, 0..2: plane-parallel shift along that axis, 3: radial
-    observer: tuple = (0.0, 0.0, 0.0)   # Mpc/h, box coordinates (radial shift only)
+    observer: tuple = (0.0, 0.0, 0.0)   # Mpc/h, box coordinates (radial shift, lightcone)
+    lightcone: bool = False     # observe each particle on the observer's past light cone (Appendix A)
     likelihood: str = "gaussian"   # "gaussian" (linear bias) | "poisson" (power law + sigmoid)
     bias_b: float = 1.5
     sigma: float = 1.0
@@ -167,6 +168,8 @@ def evolve(s, cfg, lnk, lnp, keep=False):
     sch = cosmo.leapfrog_schedule(cfg.a_init, cfg.n_steps, cfg.omega_m)
     f, _, _ = force(disp, cfg, ops)
     disp_k = [disp.copy()] if keep else None
+    snaps = snapshot_states(cfg) if cfg.lightcone else []
+    snap_x, snap_p = [], []
     for k in range(cfg.n_steps):
         mom = mom + sch["Ka"][k] * f
         disp = disp + sch["Dr"][k] * mom
@@ -174,7 +177,104 @@ def evolve(s, cfg, lnk, lnp, keep=False):
         mom = mom + sch["Kb"][k] * f
         if keep:
             disp_k.append(disp.copy())
-    return disp, mom, {"ops": ops, "sched": sch, "disp_k": disp_k, "lpt": lpt_info}
+        if k + 1 in snaps:   # position and (synchronised) momentum at a snapshot
+            snap_x.append(disp.copy())
+            snap_p.append(mom.copy())
+    return disp, mom, {"ops": ops, "sched": sch, "disp_k": disp_k, "lpt": lpt_info,
+                       "snap_x": snap_x, "snap_p": snap_p}
+
+
+# ---- lightcone (Sec. 2.2.1 item 3, Appendix A) -----------------------------
+SNAP_A = (0.8, 0.9, 1.0)   # scale factors of the saved snapshots
+LC_ITERATIONS = 3
+
+
+def snapshot_states(cfg):
+    """Indices k of the leapfrog states at the snapshot scale factors; the
+    uniform a grid must contain them (e.g. a_init = 0.1 with 9 or 18 steps)."""
+    a = cfg.a_init + (1.0 - cfg.a_init) / cfg.n_steps * np.arange(cfg.n_steps + 1)
+    out = []
+    for sa in SNAP_A:
+        k = int(np.argmin(np.abs(a - sa)))
+        if abs(a[k] - sa) > 1e-9:
+            raise ValueError(f"the leapfrog grid has no state at a = {sa}")
+        out.append(k)
+    return out
+
+
+def _interp_snapshots(Y, a):
+    """Linear interpolation in a between the bracketing snapshots (a clamped to
+    [0.8, 1]); returns (y, per-snapshot weights (3, M), dy/da)."""
+    sa = np.asarray(SNAP_A)
+    ac = np.clip(a, sa[0], sa[-1])
+    j = np.where(ac <= sa[1], 0, 1)
+    t = (ac - sa[j]) / (sa[j + 1] - sa[j])
+    w = np.zeros((3, a.size))
+    idx = np.arange(a.size)
+    w[j, idx] += 1.0 - t
+    w[j + 1, idx] += t
+    y = np.einsum("sm,smc->mc", w, Y)
+    inside = ((a >= sa[0]) & (a <= sa[-1]))[:, None]
+    dy = np.where(inside, (Y[j + 1, idx] - Y[j, idx]) / (sa[j + 1] - sa[j])[:, None], 0.0)
+    return y, w, dy
+
+
+def _lightcone_forward(X, P, cfg, tab):
+    q = M.lattice_cells(cfg.n) * cfg.cell
+    o = np.asarray(cfg.observer, np.float64)
+    a = np.ones(q.shape[0])
+    hist = []
+    for _ in range(LC_ITERATIONS):   # a^(n) = DistToScaleFactor(|x(a^(n-1)) - o|), a^(0) = 1
+        x, w, dx = _interp_snapshots(X, a)
+        r = q + x - o
+        d = np.sqrt(np.sum(r * r, axis=1))
+        a_new, slope = cosmo.dist_to_scale_factor(d, *tab)
+        hist.append((w, dx, r, d, slope))
+        a = a_new
+    x, wx, dx = _interp_snapshots(X, a)
+    p, _, dp = _interp_snapshots(P, a)
+    r = q + x - o
+    rn = np.sqrt(np.sum(r * r, axis=1))
+    u = r / rn[:, None]
+    e = cosmo.efunc(a, cfg.omega_m)
+    s = 1.0 / (a * a * e)
+    pu = np.sum(p * u, axis=1)
+    obs = x + (s * pu)[:, None] * u
+    return obs, {"a": a, "hist": hist, "wx": wx, "dx": dx, "dp": dp, "p": p, "u": u, "rn": rn, "s": s,
+                 "pu": pu, "e": e}
+
+
+def lightcone_observed(X, P, cfg, tab):
+    """Displacement of each particle as observed on the light cone: scale
+    factor a_i from three fixed-point iterations of DistToScaleFactor starting
+    at a = 1, position and momentum interpolated to a_i between the snapshots,
+    then the radial redshift-space shift (p . d) d / (a_i^2 E(a_i))."""
+    return _lightcone_forward(np.asarray(X), np.asarray(P), cfg, tab)[0]
+
+
+def lightcone_vjp(X, P, obsbar, cfg, tab):
+    """Transpose of the Jacobian of lightcone_observed wrt the snapshots
+    (X, P), applied to the cotangent of the observed displacement."""
+    X, P = np.asarray(X), np.asarray(P)
+    _, c = _lightcone_forward(X, P, cfg, tab)
+    a, u, rn, s, pu, p = c["a"], c["u"], c["rn"], c["s"], c["pu"], c["p"]
+    ux = np.sum(u * obsbar, axis=1)
+    proj = lambda v: v - u * np.sum(u * v, axis=1)[:, None]
+    pbar = (s * ux)[:, None] * u
+    xbar = obsbar + (s / rn)[:, None] * (proj(p) * ux[:, None] + pu[:, None] * proj(obsbar))
+    # d s / d a with s = 1/(a^2 E), dE/da = -1.5 Omega_m a^-4 / E
+    e = c["e"]
+    de = -1.5 * cfg.omega_m * a ** -4 / e
+    ds = -2.0 / (a ** 3 * e) - de / (a * a * e * e)
+    abar = ds * pu * ux + np.sum(xbar * c["dx"], axis=1) + np.sum(pbar * c["dp"], axis=1)
+    Xbar = np.einsum("sm,mc->smc", c["wx"], xbar)
+    Pbar = np.einsum("sm,mc->smc", c["wx"], pbar)
+    for w, dx, r, d, slope in reversed(c["hist"]):
+        rbar = (abar * slope / d)[:, None] * r
+        Xbar += np.einsum("sm,mc->smc", w, rbar)
+        abar = np.sum(rbar * dx, axis=1)
+    return Xbar, Pbar
+
 
 
 def rsd_coefficient(cfg):
@@ -261,8 +361,12 @@ def likelihood_terms(delta, data, resp, cfg):
 
 def loss(s, cfg, lnk, lnp, data, resp):
     """Total loss = -log L + (w/2) sum s^2.  Returns (loss, parts dict)."""
-    disp, mom, _ = evolve(s, cfg, lnk, lnp)
-    delta = final_density(observed_positions(disp, mom, cfg), cfg)
+    disp, mom, ev = evolve(s, cfg, lnk, lnp)
+    if cfg.lightcone:
+        obs = lightcone_observed(ev["snap_x"], ev["snap_p"], cfg, cosmo.distance_table(cfg.omega_m))
+    else:
+        obs = observed_positions(disp, mom, cfg)
+    delta = final_density(obs, cfg)
     lik, _ = likelihood_terms(delta, data, resp, cfg)
     prior = 0.5 * cfg.prior_weight * float(np.sum(np.asarray(s, np.float64) ** 2))
     return lik + prior, {"likelihood": lik, "prior": prior, "delta": delta,
@@ -280,7 +384,11 @@ def gradient(s, cfg, lnk, lnp, data, resp, loss_weight=1.0, cot_delta=None):
     n = cfg.n
     disp, mom, info = evolve(s, cfg, lnk, lnp, keep=True)
     ops, sch, disp_k = info["ops"], info["sched"], info["disp_k"]
-    obs = observed_positions(disp, mom, cfg)
+    if cfg.lightcone:
+        tab = cosmo.distance_table(cfg.omega_m)
+        obs = lightcone_observed(info["snap_x"], info["snap_p"], cfg, tab)
+    else:
+        obs = observed_positions(disp, mom, cfg)
     delta = final_density(obs, cfg)
     lik, dlik = likelihood_terms(delta, data, resp, cfg)
     prior = 0.5 * cfg.prior_weight * float(np.sum(s * s))
@@ -291,9 +399,21 @@ def gradient(s, cfg, lnk, lnp, data, resp, loss_weight=1.0, cot_delta=None):
         dbar = dbar + cot_delta
     # final paint: delta = paint(u_obs) - 1
     xsbar = M.cic_readout_grad(positions_cells(obs, cfg), dbar) / cfg.cell
-    xbar, pbar = observed_positions_vjp(disp, mom, xsbar, cfg)
+    if cfg.lightcone:
+        # the observed field depends on the snapshot states: their cotangents
+        # join the reverse sweep at those states
+        Xbar, Pbar = lightcone_vjp(info["snap_x"], info["snap_p"], xsbar, cfg, tab)
+        snaps = snapshot_states(cfg)
+        xbar, pbar = np.zeros_like(xsbar), np.zeros_like(xsbar)
+    else:
+        xbar, pbar = observed_positions_vjp(disp, mom, xsbar, cfg)
+        snaps = []
     # leapfrog steps in reverse
     for k in range(cfg.n_steps - 1, -1, -1):
+        if k + 1 in snaps:
+            j = snaps.index(k + 1)
+            xbar = xbar + Xbar[j]
+            pbar = pbar + Pbar[j]
         xbar = xbar + force_vjp(disp_k[k + 1], sch["Kb"][k] * pbar, cfg, ops)
         pbar = pbar + sch["Dr"][k] * xbar
         xbar = xbar + force_vjp(disp_k[k], sch["Ka"][k] * pbar, cfg, ops)

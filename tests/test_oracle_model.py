@@ -304,3 +304,86 @@ def test_radial_rsd_vjp_dot_product(table):
         lhs = np.sum(jv * w)
         rhs = np.sum(vx * xb) + np.sum(vp * pb)
         assert abs(lhs - rhs) < 1e-7 * abs(rhs)
+
+
+def test_comoving_distance_and_inverse():
+    """chi(a) for Omega_m = 1 is 2 (c/H0)(1 - sqrt(a)) (closed form); the
+    table inverse returns a to the linear-interpolation error of its grid."""
+    from oracle import cosmology as OC
+    a = np.array([0.5, 0.63, 0.8, 0.9, 0.97, 1.0])
+    np.testing.assert_allclose(OC.comoving_distance(a, 1.0), 2 * OC.C_OVER_H0 * (1 - np.sqrt(a)), rtol=1e-10,
+                               atol=1e-9)
+    at, ct = OC.distance_table(0.25)
+    aa = np.linspace(0.52, 0.999, 37)
+    back, slope = OC.dist_to_scale_factor(OC.comoving_distance(aa, 0.25), at, ct)
+    assert np.abs(back - aa).max() < 1e-7
+    # slope = 1 / (dchi/da) = -a^2 E / (c/H0)
+    np.testing.assert_allclose(slope, -aa ** 2 * OC.efunc(aa, 0.25) / OC.C_OVER_H0, rtol=2e-3)
+
+
+def test_lightcone_static_snapshots_closed_form():
+    """With identical snapshots the observed displacement is the snapshot plus
+    the radial shift at a_i = DistToScaleFactor(|q + x - o|)."""
+    from oracle import cosmology as OC
+    n, box = 8, 64.0
+    cfg = model.Config(n=n, box=box, lightcone=True, observer=(30.0, 40.0, -450.0))
+    rng = np.random.default_rng(8)
+    x = rng.normal(0, 1.0, (n ** 3, 3))
+    p = rng.normal(0, 2.0, (n ** 3, 3))
+    X, P = np.stack([x, x, x]), np.stack([p, p, p])
+    tab = OC.distance_table(cfg.omega_m)
+    obs = model.lightcone_observed(X, P, cfg, tab)
+    q = np.array([[i, j, l] for i in range(n) for j in range(n) for l in range(n)], float) * (box / n)
+    r = q + x - np.array(cfg.observer)
+    d = np.linalg.norm(r, axis=1)
+    a, _ = OC.dist_to_scale_factor(d, *tab)
+    assert (a > 0.8).all() and (a < 0.9).all()
+    u = r / d[:, None]
+    s = 1.0 / (a * a * OC.efunc(a, cfg.omega_m))
+    np.testing.assert_allclose(obs, x + (s * np.sum(p * u, axis=1))[:, None] * u, rtol=1e-12, atol=1e-12)
+
+
+def test_lightcone_vjp_dot_product():
+    """<J v, w> = <v, J^T w> for the lightcone map wrt all snapshot positions
+    and momenta (iterations, interpolation and shift), central differences."""
+    from oracle import cosmology as OC
+    n, box = 8, 64.0
+    cfg = model.Config(n=n, box=box, lightcone=True, observer=(30.0, 40.0, -450.0))
+    rng = np.random.default_rng(9)
+    base = rng.normal(0, 1.0, (n ** 3, 3))
+    X = np.stack([base + rng.normal(0, 3.0, base.shape) * t for t in (0.0, 0.5, 1.0)])
+    P = rng.normal(0, 2.0, (3, n ** 3, 3))
+    tab = OC.distance_table(cfg.omega_m)
+    w = rng.standard_normal((n ** 3, 3))
+    Xb, Pb = model.lightcone_vjp(X, P, w, cfg, tab)
+    for _ in range(3):
+        vx, vp = rng.standard_normal(X.shape), rng.standard_normal(P.shape)
+        h = 1e-6
+        jv = (model.lightcone_observed(X + h * vx, P + h * vp, cfg, tab)
+              - model.lightcone_observed(X - h * vx, P - h * vp, cfg, tab)) / (2 * h)
+        lhs, rhs = np.sum(jv * w), np.sum(vx * Xb) + np.sum(vp * Pb)
+        assert abs(lhs - rhs) < 1e-6 * abs(rhs), (lhs, rhs)
+
+
+def test_lightcone_gradient_brute_force(table):
+    """Central differences on all 512 coordinates of an 8^3 lightcone case
+    (snapshots at a = 0.8, 0.9, 1 of a 9-step run, observer 450 Mpc/h away)."""
+    lnk, lnp = table
+    cfg = model.Config(n=8, box=64.0, n_steps=9, lpt_order=2, lightcone=True, observer=(30.0, 40.0, -450.0),
+                       likelihood="gaussian", bias_b=1.5, sigma=1.0, prior_weight=1.0)
+    n = cfg.n
+    s = inputs.white_noise(n, 41).astype(np.float64)
+    data = inputs.normal_field(n, 42).astype(np.float64)
+    resp = np.ones((n, n, n))
+    f0, g, _ = model.gradient(s, cfg, lnk, lnp, data, resp)
+    assert f0 == pytest.approx(model.loss(s, cfg, lnk, lnp, data, resp)[0], rel=1e-14)
+    eps = 1e-6
+    fd = np.empty(n ** 3)
+    for i in range(n ** 3):
+        sp, sm = s.copy(), s.copy()
+        sp.flat[i] += eps
+        sm.flat[i] -= eps
+        fd[i] = (model.loss(sp, cfg, lnk, lnp, data, resp)[0] - model.loss(sm, cfg, lnk, lnp, data, resp)[0]) / (2 * eps)
+    bad = np.abs(fd - g.reshape(-1)) > 1e-6 * np.abs(g).max() + 1e-6 * np.abs(g.reshape(-1))
+    assert np.count_nonzero(bad) <= 3
+    assert np.linalg.norm(fd - g.reshape(-1)) / np.linalg.norm(g) < 1e-6
