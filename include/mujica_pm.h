@@ -62,7 +62,11 @@ typedef struct {
   int32_t precision;        /* PM_PREC_F32 (FP32 mesh / FFT / particles, FP64 reductions) or PM_PREC_F64 */
   int32_t checkpoint_every; /* 0: pm_adjoint keeps every step's particle state; c > 0: keeps (x, p)
                                every c steps and recomputes the steps in between (same result) */
-  int32_t reserved0;
+  int32_t lightcone;        /* 1: observe each particle on the observer's past light cone (Appendix A):
+                               snapshots at a = 0.8, 0.9, 1 (the uniform step grid must hold them, e.g.
+                               a_init = 0.1 with 9 or 18 steps), scale factor from three fixed-point
+                               iterations of DistToScaleFactor, linear interpolation between snapshots,
+                               radial shift at that scale factor; needs rsd_axis = 3.  0: off */
   double box;               /* side of the periodic box, Mpc/h */
   double omega_m;           /* flat LCDM matter density (E(a) and the Poisson source) */
   double a_init;            /* scale factor of the 2LPT initial condition, 0 < a_init < 1 */
@@ -106,6 +110,13 @@ pm_status pm_linear_power_table(double omega_m, double omega_b, double h, double
  * kick / drift factors (Sec. 2.2.1 item 2).  Any output may be NULL. */
 pm_status pm_growth(double omega_m, int32_t n_a, const double *a, double *D1, double *D2,
                     double *Gp1, double *Gp2);
+
+/* Comoving distance table of the lightcone (Appendix A, DistToScaleFactor):
+ * a_j = a_min + j (1 - a_min) / (n - 1) and chi_j = (c/H0) int_{a_j}^1 da / (a^2 E(a))
+ * in Mpc/h, j = 0..n-1 (host arrays of n >= 2 doubles, caller-owned).  A plan with
+ * lightcone = 1 builds this table with a_min = 0.5, n = 2049.  Errors:
+ * PM_ERR_INVALID_ARG (NULL output, n < 2, a_min outside (0, 1), omega_m outside (0, 1]). */
+pm_status pm_distance_table(double omega_m, double a_min, int32_t n, double *a, double *chi);
 
 /* ---- plan: the forward model and its adjoint --------------------------- */
 

@@ -28,7 +28,7 @@ class pm_config(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("lpt_order", ctypes.c_int32),
         ("rsd_axis", ctypes.c_int32), ("likelihood", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("checkpoint_every", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("checkpoint_every", ctypes.c_int32), ("lightcone", ctypes.c_int32),
         ("box", ctypes.c_double), ("omega_m", ctypes.c_double), ("a_init", ctypes.c_double),
         ("bias_b", ctypes.c_double), ("sigma", ctypes.c_double), ("alpha", ctypes.c_double),
         ("delta_th", ctypes.c_double), ("K", ctypes.c_double), ("nbar_cell", ctypes.c_double),
@@ -55,6 +55,7 @@ SIGNATURES = {
     "pm_launch_count": (ctypes.c_int64, []),
     "pm_linear_power_table": (_I32, [_D, _D, _D, _D, _D, _D, _D, _I32, _DP, _DP]),
     "pm_growth": (_I32, [_D, _I32, _DP, _DP, _DP, _DP, _DP]),
+    "pm_distance_table": (_I32, [_D, _D, _I32, _DP, _DP]),
     "pm_workspace_bytes": (_I32, [_CFGP, _SZP]),
     "pm_plan_create": (_I32, [_CFGP, _DP, _DP, _I32, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "pm_plan_destroy": (_I32, [_P]),

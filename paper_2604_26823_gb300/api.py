@@ -52,6 +52,7 @@ class Config:
     rho_floor: float = 1e-3
     prior_weight: float = 1.0
     observer: tuple = (0.0, 0.0, 0.0)  # Mpc/h, box coordinates (rsd_axis = 3)
+    lightcone: bool = False            # observe on the past light cone (needs rsd_axis = 3)
 
     def to_c(self):
         c = L.pm_config()
@@ -59,6 +60,7 @@ class Config:
         c.likelihood = {"gaussian": L.PM_LIK_GAUSSIAN, "poisson": L.PM_LIK_POISSON}[self.likelihood]
         c.precision = {"f32": L.PM_PREC_F32, "f64": L.PM_PREC_F64}[self.precision]
         c.checkpoint_every = self.checkpoint_every
+        c.lightcone = 1 if self.lightcone else 0
         for f in ("box", "omega_m", "a_init", "bias_b", "sigma", "alpha", "delta_th", "K",
                   "nbar_cell", "rho_floor", "prior_weight"):
             setattr(c, f, float(getattr(self, f)))
@@ -81,6 +83,16 @@ def pm_linear_power_table(omega_m=0.25, omega_b=0.045, h=0.73, sigma8=0.9, n_s=1
                                       lnk.ctypes.data_as(L._DP), lnp.ctypes.data_as(L._DP)),
             "pm_linear_power_table")
     return lnk, lnp
+
+
+def pm_distance_table(omega_m, a_min=0.5, n=2049):
+    """Host table (a_j, chi_j) of the lightcone's comoving distances (library host code)."""
+    lib = L.load()
+    a = np.zeros(n)
+    chi = np.zeros(n)
+    L.check(lib.pm_distance_table(omega_m, a_min, n, a.ctypes.data_as(L._DP), chi.ctypes.data_as(L._DP)),
+            "pm_distance_table")
+    return a, chi
 
 
 def pm_growth(omega_m, a):

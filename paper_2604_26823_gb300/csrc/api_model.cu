@@ -52,6 +52,17 @@ pm_status pm_validate_config(const pm_config *c) {
     pm::set_error("radial redshift-space shift needs a finite observer position");
     return PM_ERR_INVALID_ARG;
   }
+  if (c->lightcone != 0) {
+    if (c->lightcone != 1 || c->rsd_axis != 3) {
+      pm::set_error("lightcone must be 0 or 1, and the lightcone needs rsd_axis = 3 (radial)");
+      return PM_ERR_INVALID_ARG;
+    }
+    int ks[2];
+    if (!pm::lightcone_states(*c, ks)) {
+      pm::set_error("lightcone: the uniform step grid has no state at a = 0.8 or a = 0.9");
+      return PM_ERR_UNSUPPORTED;
+    }
+  }
   if (c->likelihood == PM_LIK_GAUSSIAN && !(c->sigma > 0)) {
     pm::set_error("Gaussian likelihood needs sigma > 0");
     return PM_ERR_INVALID_ARG;
@@ -99,6 +110,15 @@ pm_status pm_growth(double omega_m, int32_t n_a, const double *a, double *D1, do
     if (Gp1) Gp1[i] = g[i].Gp1;
     if (Gp2) Gp2[i] = g[i].Gp2;
   }
+  return PM_OK;
+}
+
+pm_status pm_distance_table(double omega_m, double a_min, int32_t n, double *a, double *chi) {
+  if (!a || !chi || n < 2 || !(a_min > 0) || !(a_min < 1) || !(omega_m > 0) || !(omega_m <= 1)) {
+    pm::set_error("invalid distance table arguments");
+    return PM_ERR_INVALID_ARG;
+  }
+  pmhost::distance_table(omega_m, a_min, n, a, chi);
   return PM_OK;
 }
 

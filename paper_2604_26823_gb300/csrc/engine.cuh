@@ -125,8 +125,25 @@ template <typename T> struct OutGrad {  // out = v + w * s
 static __global__ void k_set_int(int *p, int v) { *p = v; }
 
 // ---- workspace layout -----------------------------------------------------
+// Leapfrog states holding the lightcone snapshots at a = 0.8 and 0.9 (the
+// one at a = 1 is the final state n_steps); false when the uniform grid
+// a_k = a_init + k (1 - a_init) / n_steps has no state there.
+constexpr int kLcTable = 2049;  // distance table points, a uniform on [0.5, 1]
+inline bool lightcone_states(const pm_config &c, int (&ks)[2]) {
+  const double h = (1.0 - c.a_init) / c.n_steps;
+  const double sa[2] = {0.8, 0.9};
+  for (int j = 0; j < 2; ++j) {
+    const double kf = std::nearbyint((sa[j] - c.a_init) / h);
+    if (!(kf >= 0.0 && kf < c.n_steps)) return false;
+    ks[j] = (int)kf;
+    if (std::fabs(c.a_init + h * ks[j] - sa[j]) > 1e-9) return false;
+  }
+  return true;
+}
+
 struct Layout {
-  size_t tw, amp, spec, fx, psi, psi2, src, dbar, mom, xbar, pbar, disp, phi, ckd, ckm, dwork, scal, total;
+  size_t tw, amp, spec, fx, psi, psi2, src, dbar, mom, xbar, pbar, disp, phi, ckd, ckm, dwork, snap, lct, scal,
+      total;
   int nck, seglen;
 };
 
@@ -170,6 +187,11 @@ inline Layout make_layout(const pm_config &c) {
     L.ckm = take((size_t)L.nck * 3 * m * es);
     L.dwork = take(3 * m * es);
   }
+  L.snap = L.lct = 0;
+  if (c.lightcone) {
+    L.snap = take(12 * m * es);             // X_0, X_1, P_0, P_1 (then their cotangents)
+    L.lct = take(3 * kLcTable * es);        // a_j, chi_j, slope_j
+  }
   L.scal = take(64 * 1024);
   L.total = off;
   return L;
@@ -184,6 +206,10 @@ template <typename T> struct Engine {
   int64_t M = 0, S = 0;
   double cell = 0, kf = 0;
   std::vector<double> ck, dr;  // merged kick factors c_0..c_n and drifts
+  std::vector<double> kbv;     // kbv[k] = Kb_{k-1}: second half-kick of the step into state k
+  bool lc_on = false, lc_write = true;
+  int lc_k[2] = {-1, -1};      // states of the snapshots at a = 0.8, 0.9
+  T *snap = nullptr, *lct = nullptr;
   double d1 = 0, d2 = 0, gp1 = 0, gp2 = 0, rsd = 0;
   int rho_exp = 0;
   std::vector<int64_t> rom_counts;
@@ -205,6 +231,18 @@ template <typename T> struct Engine {
   Profiler prof;
 
   T obs_cell(int a) const { return (T)(cfg.observer[a] / cell); }  // observer in cell units
+  part::LightCone<T> lightcone() const {
+    part::LightCone<T> l{};
+    l.snap = snap;
+    l.ta = lct;
+    l.tchi = lct + kLcTable;
+    l.tsl = lct + 2 * kLcTable;
+    l.ntab = kLcTable;
+    l.om = (T)cfg.omega_m;
+    l.cell = (T)cell;
+    for (int a = 0; a < 3; ++a) l.o[a] = obs_cell(a);
+    return l;
+  }
   part::Geo geo() const {
     part::Geo g;
     g.L.logn = logn;
@@ -248,6 +286,15 @@ template <typename T> struct Engine {
       ckm = reinterpret_cast<T *>(base + lay.ckm);
       dwork = reinterpret_cast<T *>(base + lay.dwork);
     }
+    lc_on = c.lightcone != 0;
+    if (lc_on) {
+      snap = reinterpret_cast<T *>(base + lay.snap);
+      lct = reinterpret_cast<T *>(base + lay.lct);
+      if (!lightcone_states(c, lc_k)) {
+        set_error("lightcone: the uniform step grid has no state at a = 0.8 or a = 0.9");
+        return PM_ERR_UNSUPPORTED;
+      }
+    }
     char *sc = base + lay.scal;
     partial = reinterpret_cast<double *>(sc);
     results = partial + pw::kRedBlocks;
@@ -267,6 +314,8 @@ template <typename T> struct Engine {
       ck[k] = v;
     }
     for (int k = 0; k < ns; ++k) dr[k] = sch.Dr[k];
+    kbv.assign(ns + 1, 0.0);
+    for (int k = 1; k <= ns; ++k) kbv[k] = sch.Kb[k - 1];
     d1 = sch.lpt.D1;
     d2 = c.lpt_order == 2 ? sch.lpt.D2 : 0.0;
     gp1 = sch.lpt.Gp1;
@@ -282,6 +331,18 @@ template <typename T> struct Engine {
     }
     PM_CUDA_TRY(cudaMemcpy(tw, h_tw.data(), n * sizeof(C), cudaMemcpyHostToDevice));
     PM_CUDA_TRY(cudaMemset(maxslots, 0, part::kMaxSlots * sizeof(unsigned long long)));
+    if (lc_on) {
+      // distance table (host FP64), with the slope of each interval taken in FP64
+      std::vector<double> ta(kLcTable), tc(kLcTable);
+      pmhost::distance_table(c.omega_m, 0.5, kLcTable, ta.data(), tc.data());
+      std::vector<T> h(3 * kLcTable, T(0));
+      for (int j = 0; j < kLcTable; ++j) {
+        h[j] = (T)ta[j];
+        h[kLcTable + j] = (T)tc[j];
+        if (j + 1 < kLcTable) h[2 * kLcTable + j] = (T)((ta[j] - ta[j + 1]) / (tc[j] - tc[j + 1]));
+      }
+      PM_CUDA_TRY(cudaMemcpy(lct, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
     // IC amplitude (table staged in the spectrum buffer)
     if ((size_t)npk * 16 > (size_t)S * sizeof(C)) {
       set_error("power table too large for this mesh");
@@ -522,8 +583,14 @@ template <typename T> struct Engine {
       PM_TRY(memset_fx(1));
       {
         ProfScope ps(prof, P_KDK, st, (double)M * (16 * sizeof(T) + 8));
-        PM_TRY(deposit(part::SrcKdk<T>{g.L, M, pstate(si), dstate(si), dstate(so), momb, (T)ck[k], (T)dr[k],
-                                           fx_exp, T(0)}));
+        part::SrcKdk<T> src_k{g.L, M, pstate(si), dstate(si), dstate(so), momb, (T)ck[k], (T)dr[k], fx_exp, T(0)};
+        if (lc_on && lc_write && (k == lc_k[0] || k == lc_k[1])) {
+          const int j = k == lc_k[0] ? 0 : 1;
+          src_k.snap_x = snap + (int64_t)j * 3 * M;
+          src_k.snap_p = snap + (int64_t)(2 + j) * 3 * M;
+          src_k.kb = (T)kbv[k];
+        }
+        PM_TRY(deposit(src_k));
       }
       PM_TRY(force_mesh(pstate(so)));
     }
@@ -560,8 +627,13 @@ template <typename T> struct Engine {
     }
     const int fin = (keep && keep_all()) ? ns : 0;
     PM_TRY(memset_fx(1));
-    return deposit(part::SrcFinal<T>{geo().L, M, pstate(fin), dstate(fin), mom, (T)ck[ns], cfg.rsd_axis, (T)rsd,
-                                     fx_exp, T(0), {obs_cell(0), obs_cell(1), obs_cell(2)}});
+    part::SrcFinal<T> fsrc{geo().L, M, pstate(fin), dstate(fin), mom, (T)ck[ns], cfg.rsd_axis, (T)rsd,
+                           fx_exp, T(0), {obs_cell(0), obs_cell(1), obs_cell(2)}};
+    if (lc_on) {
+      fsrc.lightcone = true;
+      fsrc.lc = lightcone();
+    }
+    return deposit(fsrc);
   }
 
   pm_status loss_terms(const T *s, const T *data, const T *R, const T *cot, double lw, bool want_dbar,
@@ -663,6 +735,31 @@ template <typename T> struct Engine {
     return k > 0 ? fold_max() : PM_OK;
   }
 
+  // reverse_step, with the cotangents (Xbar_j, Pbar_j) of a lightcone snapshot
+  // held at state k joined in.  The snapshot momentum mom + kb F(x_k) shares
+  // the force F(x_k) with the merged kick c_k, so before the step
+  // pbar += (kb / c_k) Pbar_j makes its cotangent paint c_k pbar + kb Pbar_j,
+  // and after it pbar += (1 - kb / c_k) Pbar_j completes the cotangent of the
+  // momentum before the kick (then the running max is taken again).
+  pm_status reverse_step_lc(int k, const T *xk, const V4<T> *phik) {
+    const int j = !lc_on ? -1 : (k == lc_k[0] ? 0 : (k == lc_k[1] ? 1 : -1));
+    if (j < 0) return reverse_step(k, xk, phik);
+    const part::Geo g = geo();
+    const int nb = grid_for(M, 256);
+    const T *xb = snap + (int64_t)j * 3 * M, *pb = snap + (int64_t)(2 + j) * 3 * M;
+    const double f = kbv[k] / ck[k];
+    ::pm::note_launch();
+    part::k_lc_join<T><<<nb, 256, 0, st>>>(g, xbar, pbar, xb, pb, (T)f, (T)ck[k], maxslots);
+    PM_LAUNCH_CHECK();
+    PM_TRY(fold_max());
+    PM_TRY(reverse_step(k, xk, phik));
+    ::pm::note_launch();
+    part::k_lc_join<T><<<nb, 256, 0, st>>>(g, nullptr, pbar, nullptr, pb, (T)(1.0 - f),
+                                            k > 0 ? (T)ck[k - 1] : T(0), maxslots);
+    PM_LAUNCH_CHECK();
+    return fold_max();
+  }
+
   pm_status adjoint(const T *s, const T *data, const T *R, double lw, const T *cot, double *loss_out,
                     T *grad) {
     const int ns = cfg.n_steps;
@@ -673,12 +770,19 @@ template <typename T> struct Engine {
     // final paint + RSD
     const T *xn = keep_all() ? dstate(ns) : dwork;
     ::pm::note_launch();
-    part::k_adj_final<T><<<nb, 256, 0, st>>>(g, xn, mom, cfg.rsd_axis, (T)rsd, obs_cell(0), obs_cell(1), obs_cell(2),
-                                              dbar, xbar, pbar, (T)ck[ns], maxslots);
+    if (lc_on) {
+      // cotangents of the final state into (xbar, pbar), of the other two
+      // snapshots over the snapshot buffer
+      part::k_adj_final_lc<T><<<nb, 256, 0, st>>>(g, lightcone(), snap, xn, mom, dbar, xbar, pbar, (T)ck[ns],
+                                                   maxslots);
+    } else {
+      part::k_adj_final<T><<<nb, 256, 0, st>>>(g, xn, mom, cfg.rsd_axis, (T)rsd, obs_cell(0), obs_cell(1),
+                                                obs_cell(2), dbar, xbar, pbar, (T)ck[ns], maxslots);
+    }
     PM_LAUNCH_CHECK();
     PM_TRY(fold_max());
     if (keep_all()) {
-      for (int k = ns; k >= 0; --k) PM_TRY(reverse_step(k, dstate(k), pstate(k)));
+      for (int k = ns; k >= 0; --k) PM_TRY(reverse_step_lc(k, dstate(k), pstate(k)));
     } else {
       const int ce = cfg.checkpoint_every;
       for (int j = ns / ce; j >= 0; --j) {
@@ -692,8 +796,11 @@ template <typename T> struct Engine {
         PM_TRY(set_exp(0, rho_exp));
         PM_TRY(deposit(part::SrcPaint<T>{g.L, M, dstate(0), psi2, -1, T(0), fx_exp, T(0)}));
         PM_TRY(force_mesh(pstate(0)));
-        PM_TRY(run_steps(lo, hi, lo, true, psi2));
-        for (int k = hi; k >= lo; --k) PM_TRY(reverse_step(k, dstate(k - lo), pstate(k - lo)));
+        lc_write = false;  // the snapshot buffer holds their cotangents now
+        const pm_status rs = run_steps(lo, hi, lo, true, psi2);
+        lc_write = true;
+        PM_TRY(rs);
+        for (int k = hi; k >= lo; --k) PM_TRY(reverse_step_lc(k, dstate(k - lo), pstate(k - lo)));
       }
     }
     PM_TRY(lpt_adjoint(s, lw, grad));

@@ -147,4 +147,28 @@ void power_table(double om, double ob, double h, double sigma8, double ns, doubl
   }
 }
 
+void distance_table(double om, double a_min, int n, double *a, double *chi) {
+  // 8-point Gauss-Legendre on each grid interval (the integrand is smooth on
+  // [a_min, 1], so each interval's rule is exact to rounding), accumulated
+  // from a = 1 downward
+  static const double xg[4] = {0.18343464249564980494, 0.52553240991632898582, 0.79666647741362673959,
+                               0.96028985649753623168};
+  static const double wg[4] = {0.36268378337836198297, 0.31370664587788728734, 0.22238103445337447054,
+                               0.10122853629037625915};
+  const double da = (1.0 - a_min) / (n - 1);
+  for (int j = 0; j < n; ++j) a[j] = j == n - 1 ? 1.0 : a_min + j * da;
+  chi[n - 1] = 0.0;
+  for (int j = n - 2; j >= 0; --j) {
+    const double lo = a[j], hi = a[j + 1], mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+    double s = 0.0;
+    for (int g = 0; g < 4; ++g) {
+      for (int sg = -1; sg <= 1; sg += 2) {
+        const double x = mid + sg * half * xg[g];
+        s += wg[g] / (x * x * efunc(x, om));
+      }
+    }
+    chi[j] = chi[j + 1] + kCOverH0 * half * s;
+  }
+}
+
 }  // namespace pmhost

@@ -268,12 +268,24 @@ template <typename T> struct SrcKdk {
   T kick, drift;
   const int *fx_exp;
   T scale;
+  // lightcone snapshot of this state (null: none): position, and the momentum
+  // synchronised with it, mom + kb F (kb: second half-kick of the previous step)
+  T *snap_x = nullptr, *snap_p = nullptr;
+  T kb = T(0);
   __device__ void setup() { scale = pow2<T>(__ldg(fx_exp)); }
   __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
     const T x0 = x[p], x1 = x[np + p], x2 = x[2 * np + p];
     c = locate<T>(L, p, x0, x1, x2);
     T f0, f1, f2;
     readout3<T>(L, phi, c, f0, f1, f2);
+    if (snap_x) {
+      snap_x[p] = x0;
+      snap_x[np + p] = x1;
+      snap_x[2 * np + p] = x2;
+      snap_p[p] = mom[p] + kb * f0;
+      snap_p[np + p] = mom[np + p] + kb * f1;
+      snap_p[2 * np + p] = mom[2 * np + p] + kb * f2;
+    }
     const T p0 = mom[p] + kick * f0, p1 = mom[np + p] + kick * f1, p2 = mom[2 * np + p] + kick * f2;
     mom[p] = p0;
     mom[np + p] = p1;
@@ -324,6 +336,109 @@ __device__ __forceinline__ void rsd_shift(const Lattice &L, int64_t p, int rsd_a
   }
 }
 
+// ---- lightcone (Sec. 2.2.1 item 3, Appendix A) ---------------------------
+// Snapshots at a = 0.8, 0.9, 1: positions X_j and synchronised momenta P_j
+// (cell units; X_2, P_2 are the final state).  Each particle's scale factor on
+// the observer's past light cone comes from three fixed-point iterations
+// a <- DistToScaleFactor(Delta |node + x(a) - o|) from a = 1, x(a) linear in a
+// between the bracketing snapshots (a clamped to [0.8, 1]); its observed
+// displacement is x(a) + (p(a) . u) u / (a^2 E(a)), u the unit line of sight.
+// DistToScaleFactor interpolates the table (a_j, chi_j) linearly in chi.
+constexpr int kLcIter = 3;
+template <typename T> struct LightCone {
+  const T *snap;        // X_0, X_1, P_0, P_1, each [3][np]
+  const T *ta, *tchi;   // table, a increasing, chi (Mpc/h) decreasing
+  const T *tsl;         // slope of each interval, da / dchi
+  int ntab;
+  T om, cell;           // Omega_m, cell size (Mpc/h)
+  T o[3];               // observer, cell units
+
+  __device__ __forceinline__ T snapv(int which, int a, int64_t np, int64_t p) const {
+    return snap[((int64_t)which * 3 + a) * np + p];
+  }
+  // a(d) and da/dd of the table interpolant, linear in chi between nodes and
+  // clamped to the table's ends (slope 0 outside)
+  __device__ __forceinline__ T d2s(T d, T &slope) const {
+    if (!(d < tchi[0])) {
+      slope = T(0);
+      return ta[0];
+    }
+    if (!(d > tchi[ntab - 1])) {
+      slope = T(0);
+      return ta[ntab - 1];
+    }
+    int lo = 0, hi = ntab - 1;  // chi decreases: chi[lo] > d > chi[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (tchi[mid] > d) lo = mid; else hi = mid;
+    }
+    slope = tsl[lo];  // (a_lo - a_hi) / (chi_lo - chi_hi), taken in FP64 on the host
+    return ta[hi] + slope * (d - tchi[hi]);
+  }
+  // y(a) between the snapshots (Y2 passed in), weights w[3] and dy/da
+  __device__ __forceinline__ void interp(T a, const T (&y0)[3], const T (&y1)[3], const T (&y2)[3], T (&y)[3],
+                                         T (&w)[3], T (&dy)[3]) const {
+    const T s0 = T(0.8), s1 = T(0.9), s2 = T(1.0);
+    const T ac = a < s0 ? s0 : (a > s2 ? s2 : a);
+    const bool first = ac <= s1;
+    const T lo = first ? s0 : s1, hi = first ? s1 : s2;
+    const T t = (ac - lo) / (hi - lo);
+    w[0] = first ? T(1) - t : T(0);
+    w[1] = first ? t : T(1) - t;
+    w[2] = first ? T(0) : t;
+    const bool inside = a >= s0 && a <= s2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      y[c] = w[0] * y0[c] + w[1] * y1[c] + w[2] * y2[c];
+      const T ya = first ? y0[c] : y1[c], yb = first ? y1[c] : y2[c];
+      dy[c] = inside ? (yb - ya) / (hi - lo) : T(0);
+    }
+  }
+};
+
+// Observed displacement of particle p on the light cone from the final state
+// (x2, p2) and the stored snapshots.
+template <typename T>
+__device__ __forceinline__ void lightcone_observed(const Lattice &L, const LightCone<T> &lc, int64_t np, int64_t p,
+                                                   const T (&x2)[3], const T (&p2)[3], T (&out)[3]) {
+  T x0[3], x1[3], q0[3], q1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    x0[c] = lc.snapv(0, c, np, p);
+    x1[c] = lc.snapv(1, c, np, p);
+    q0[c] = lc.snapv(2, c, np, p);
+    q1[c] = lc.snapv(3, c, np, p);
+  }
+  int nd[3];
+  L.node(p, nd[0], nd[1], nd[2]);
+  T a = T(1), x[3], w[3], dx[3], slope;
+  for (int it = 0; it < kLcIter; ++it) {
+    lc.interp(a, x0, x1, x2, x, w, dx);
+    T r2 = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T r = ((T)nd[c] + x[c]) - lc.o[c];
+      r2 += r * r;
+    }
+    a = lc.d2s(lc.cell * sqrt(r2), slope);
+  }
+  T pp[3], dp[3];
+  lc.interp(a, x0, x1, x2, x, w, dx);
+  lc.interp(a, q0, q1, p2, pp, w, dp);
+  T r[3], r2 = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    r[c] = ((T)nd[c] + x[c]) - lc.o[c];
+    r2 += r[c] * r[c];
+  }
+  const T inv = T(1) / sqrt(r2);
+  const T e = sqrt(lc.om / (a * a * a) + (T(1) - lc.om));
+  const T sh = T(1) / (a * a * e);
+  const T pu = (pp[0] * r[0] + pp[1] * r[1] + pp[2] * r[2]) * inv;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c] = x[c] + sh * pu * (r[c] * inv);
+}
+
 template <typename T> struct SrcFinal {
   static constexpr int NCH = 1;
   Lattice L;
@@ -337,6 +452,8 @@ template <typename T> struct SrcFinal {
   const int *fx_exp;
   T scale;
   T obs[3];  // observer, cell units (rsd_axis = 3)
+  bool lightcone = false;
+  LightCone<T> lc{};
   __device__ void setup() { scale = fx_exp ? pow2<T>(__ldg(fx_exp)) : T(0); }
   __device__ bool operator()(int64_t p, Cell<T> &c, T (&v)[1]) const {
     T d[3] = {x[p], x[np + p], x[2 * np + p]};
@@ -349,7 +466,11 @@ template <typename T> struct SrcFinal {
       m[a] = mom[a * np + p] + kick * f[a];
       mom[a * np + p] = m[a];
     }
-    rsd_shift<T>(L, p, rsd_axis, rsd, obs, m, d);
+    if (lightcone) {
+      lightcone_observed<T>(L, lc, np, p, d, m, d);
+    } else {
+      rsd_shift<T>(L, p, rsd_axis, rsd, obs, m, d);
+    }
     c = locate<T>(L, p, d[0], d[1], d[2]);
     v[0] = scale;
     return fx_exp != nullptr;
@@ -496,6 +617,147 @@ __global__ void k_adj_final(Geo g, const T *__restrict__ x, const T *__restrict_
       xbar[a * g.np + p] = xb[a];
       pbar[a * g.np + p] = pb[a];
       mx = max(mx, fabs(cn * pb[a]));
+    }
+  }
+  block_max_to_slots<T>(mx, maxslot);
+}
+
+// Adjoint of the final paint on the light cone (the transpose of
+// lightcone_observed): per particle, the forward iterations are repeated
+// (their inputs a and slopes kept), the paint's gradient g is gathered at the
+// observed position, then
+//   pbar(a) = s (u.g) u,   xbar(a) = g + (s/|r|) [P p (u.g) + (p.u) P g],
+//   abar = s'(a) (p.u)(u.g) + xbar . dx/da + pbar . dp/da,
+// Xbar_j = w_j xbar, Pbar_j = w_j pbar, and back through the iterations
+// rbar = abar (da/dd) Delta r/|r|, Xbar_j += w_j rbar, abar = rbar . dx/da.
+// Writes (Xbar_2, Pbar_2) to (xbar, pbar) and (Xbar_0, Xbar_1, Pbar_0,
+// Pbar_1) over the snapshots in snapbar (= lc.snap), and the running max of
+// |cn pbar|.
+template <typename T>
+__global__ void k_adj_final_lc(Geo g, LightCone<T> lc, T *snapbar, const T *__restrict__ x,
+                               const T *__restrict__ mom, const T *__restrict__ dbar, T *__restrict__ xbar,
+                               T *__restrict__ pbar, T cn, unsigned long long *maxslot) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t np = g.np;
+  T mx = T(0);
+  if (p < np) {
+    T x0[3], x1[3], x2[3], q0[3], q1[3], q2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x0[c] = lc.snapv(0, c, np, p);
+      x1[c] = lc.snapv(1, c, np, p);
+      q0[c] = lc.snapv(2, c, np, p);
+      q1[c] = lc.snapv(3, c, np, p);
+      x2[c] = x[c * np + p];
+      q2[c] = mom[c * np + p];
+    }
+    int nd[3];
+    g.L.node(p, nd[0], nd[1], nd[2]);
+    T ain[kLcIter], sl[kLcIter];
+    T a = T(1), xx[3], w[3], dx[3];
+    for (int it = 0; it < kLcIter; ++it) {
+      ain[it] = a;
+      lc.interp(a, x0, x1, x2, xx, w, dx);
+      T r2 = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T r = ((T)nd[c] + xx[c]) - lc.o[c];
+        r2 += r * r;
+      }
+      a = lc.d2s(lc.cell * sqrt(r2), sl[it]);
+    }
+    T pp[3], dp[3], wf[3];
+    lc.interp(a, x0, x1, x2, xx, wf, dx);
+    lc.interp(a, q0, q1, q2, pp, w, dp);
+    T r[3], r2 = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r[c] = ((T)nd[c] + xx[c]) - lc.o[c];
+      r2 += r[c] * r[c];
+    }
+    const T inv = T(1) / sqrt(r2);
+    T u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = r[c] * inv;
+    const T e = sqrt(lc.om / (a * a * a) + (T(1) - lc.om));
+    const T s = T(1) / (a * a * e);
+    const T pu = pp[0] * u[0] + pp[1] * u[1] + pp[2] * u[2];
+    T ob[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ob[c] = xx[c] + s * pu * u[c];
+    const Cell<T> cl = locate<T>(g.L, p, ob[0], ob[1], ob[2]);
+    T gg[3];
+    grad_gather<T>(g.L, nullptr, dbar, cl, T(0), T(0), T(0), gg[0], gg[1], gg[2]);
+    const T ug = u[0] * gg[0] + u[1] * gg[1] + u[2] * gg[2];
+    T xb[3], pb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pb[c] = s * u[c] * ug;
+      xb[c] = gg[c] + s * inv * ((pp[c] - u[c] * pu) * ug + pu * (gg[c] - u[c] * ug));
+    }
+    // s = 1/(a^2 E), dE/da = -1.5 Omega_m a^-4 / E
+    const T de = T(-1.5) * lc.om / (a * a * a * a * e);
+    const T ds = T(-2) / (a * a * a * e) - de / (a * a * e * e);
+    T abar = ds * pu * ug;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) abar += xb[c] * dx[c] + pb[c] * dp[c];
+    T X0[3], X1[3], X2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      X0[c] = wf[0] * xb[c];
+      X1[c] = wf[1] * xb[c];
+      X2[c] = wf[2] * xb[c];
+    }
+    for (int it = kLcIter - 1; it >= 0; --it) {
+      lc.interp(ain[it], x0, x1, x2, xx, w, dx);
+      T rr[3], q2s = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rr[c] = ((T)nd[c] + xx[c]) - lc.o[c];
+        q2s += rr[c] * rr[c];
+      }
+      const T f = abar * sl[it] * lc.cell / sqrt(q2s);
+      T nb = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T rb = f * rr[c];
+        X0[c] += w[0] * rb;
+        X1[c] += w[1] * rb;
+        X2[c] += w[2] * rb;
+        nb += rb * dx[c];
+      }
+      abar = nb;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      snapbar[(0 * 3 + c) * np + p] = X0[c];
+      snapbar[(1 * 3 + c) * np + p] = X1[c];
+      snapbar[(2 * 3 + c) * np + p] = wf[0] * pb[c];
+      snapbar[(3 * 3 + c) * np + p] = wf[1] * pb[c];
+      xbar[c * np + p] = X2[c];
+      const T p2b = wf[2] * pb[c];
+      pbar[c * np + p] = p2b;
+      mx = max(mx, fabs(cn * p2b));
+    }
+  }
+  block_max_to_slots<T>(mx, maxslot);
+}
+
+// Joins a snapshot's cotangents into the reverse sweep: xbar += xb (when
+// given), pbar += f pb; then the running max of |cmax pbar|.
+template <typename T>
+__global__ void k_lc_join(Geo g, T *__restrict__ xbar, T *__restrict__ pbar, const T *__restrict__ xb,
+                          const T *__restrict__ pb, T f, T cmax, unsigned long long *maxslot) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  T mx = T(0);
+  if (p < g.np) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t i = c * g.np + p;
+      if (xbar) xbar[i] += xb[i];
+      const T v = pbar[i] + f * pb[i];
+      pbar[i] = v;
+      mx = max(mx, fabs(cmax * v));
     }
   }
   block_max_to_slots<T>(mx, maxslot);

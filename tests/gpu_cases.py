@@ -31,6 +31,12 @@ CASES = {
     "radial64": dict(n=64, box=125.0, n_steps=4, lpt_order=2, rsd_axis=3, observer=(62.5, 62.5, -60.0),
                      likelihood="poisson", nbar_cell=0.5, alpha=0.7, delta_th=1.2, K=3.0, rho_floor=1e-3,
                      prior_weight=1.0),
+    # observed on the past light cone (snapshots at a = 0.8, 0.9, 1 of a 9-step
+    # run from a = 0.1; the box spans comoving distances 260-400 Mpc/h, across
+    # the a = 0.9 snapshot), 32^3 in 128 Mpc/h, linear bias
+    "lightcone32": dict(n=32, box=128.0, n_steps=9, lpt_order=2, rsd_axis=3, lightcone=True,
+                        observer=(64.0, 64.0, -260.0), likelihood="gaussian", bias_b=1.5, sigma=1.0,
+                        prior_weight=1.0),
     # Zel'dovich start, RSD along x, 16^3 (single-tile meshes)
     "tiny": dict(n=16, box=48.0, n_steps=3, lpt_order=1, rsd_axis=0, likelihood="gaussian",
                  bias_b=1.2, sigma=0.8, prior_weight=0.5),
@@ -38,7 +44,8 @@ CASES = {
 
 
 def oracle_config(kw):
-    keys = ("n", "box", "n_steps", "lpt_order", "rsd_axis", "observer", "likelihood", "bias_b", "sigma", "alpha",
+    keys = ("n", "box", "n_steps", "lpt_order", "rsd_axis", "observer", "lightcone", "likelihood", "bias_b", "sigma",
+            "alpha",
             "delta_th", "K", "nbar_cell", "rho_floor", "prior_weight")
     return OM.Config(**{k: kw[k] for k in keys if k in kw})
 

@@ -85,6 +85,32 @@ def test_host_growth_matches_oracle(lib):
             np.testing.assert_allclose(got[k], ref[k], rtol=1e-10)
 
 
+def test_host_distance_table_matches_oracle(lib):
+    from paper_2604_26823_gb300 import api
+    for om in (0.25, 0.3):
+        a, chi = api.pm_distance_table(om, 0.5, 257)
+        ra, rchi = C.distance_table(om, 0.5, 257)
+        np.testing.assert_allclose(a, ra, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(chi, rchi, rtol=1e-12, atol=1e-10)
+
+
+def test_lightcone_validation_without_gpu(lib):
+    from paper_2604_26823_gb300 import api
+    nb = ctypes.c_size_t()
+    ok = dict(n=32, box=128.0, n_steps=9, a_init=0.1, rsd_axis=3, observer=(64.0, 64.0, -260.0), lightcone=True)
+    assert lib.pm_workspace_bytes(ctypes.byref(api.Config(**ok).to_c()), ctypes.byref(nb)) == 0
+    with_lc = nb.value
+    assert lib.pm_workspace_bytes(ctypes.byref(api.Config(**dict(ok, lightcone=False)).to_c()),
+                                  ctypes.byref(nb)) == 0
+    assert with_lc - nb.value >= 12 * 32 ** 3 * 4    # four snapshot arrays of 3 x n^3
+    # no state at a = 0.8 / 0.9 on a 10-step grid from a = 0.1
+    assert lib.pm_workspace_bytes(ctypes.byref(api.Config(**dict(ok, n_steps=10)).to_c()), ctypes.byref(nb)) == 2
+    assert b"lightcone" in lib.pm_last_error()
+    # the lightcone is seen along the line of sight: rsd_axis must be 3
+    assert lib.pm_workspace_bytes(ctypes.byref(api.Config(**dict(ok, rsd_axis=2)).to_c()), ctypes.byref(nb)) == 1
+    assert lib.pm_workspace_bytes(ctypes.byref(api.Config(**dict(ok, n_steps=18)).to_c()), ctypes.byref(nb)) == 0
+
+
 def test_host_power_table_matches_oracle(lib):
     from paper_2604_26823_gb300 import api
     lnk, lnp = api.pm_linear_power_table()

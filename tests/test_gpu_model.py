@@ -113,7 +113,7 @@ def test_evolve(api, name, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-@pytest.mark.parametrize("name", ["tiny", "small", "poisson64", "rsd128", "radial64"])
+@pytest.mark.parametrize("name", ["tiny", "small", "poisson64", "rsd128", "radial64", "lightcone32"])
 def test_forward_loss_and_density(api, name, prec):
     plan = plan_for(api, name, prec)
     s, data, resp = case_inputs(name)
@@ -128,7 +128,7 @@ def test_forward_loss_and_density(api, name, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-@pytest.mark.parametrize("name", ["tiny", "small", "poisson64", "rsd128", "radial64"])
+@pytest.mark.parametrize("name", ["tiny", "small", "poisson64", "rsd128", "radial64", "lightcone32"])
 def test_gradient(api, name, prec):
     plan = plan_for(api, name, prec)
     s, data, resp = case_inputs(name)
@@ -144,8 +144,8 @@ def test_gradient(api, name, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_checkpointed_adjoint_is_bit_identical(api, prec):
-    name = "small"
+@pytest.mark.parametrize("name", ["small", "lightcone32"])
+def test_checkpointed_adjoint_is_bit_identical(api, name, prec):
     s, data, resp = case_inputs(name)
     p0 = plan_for(api, name, prec)
     out = []
