@@ -176,6 +176,28 @@ pm_status pm_evolve(pm_plan *plan, const void *s, void *disp_out, void *mom_out,
  * b delta.  out: [n^3]. */
 pm_status pm_expected_counts(pm_plan *plan, const void *s, const void *R, void *out, pm_stream_t stream);
 
+/* ---- annealing: low-resolution stage feeding the full-resolution start (Sec. 3, opening) ---- */
+
+/* White noise of the plan's mesh (n per side) from a coarse one (n_coarse per
+ * side, a power of two below n, same box): with r = n / n_coarse,
+ * out(k) = r^{3/2} s_coarse(k) on the modes with every |n_i| < n_coarse / 2 and
+ * out(k) = fresh(k) on all others, so the linear density of the coarse field
+ * (delta_L = s sqrt(P / Delta^3)) is kept and out stays unit white noise when
+ * fresh is.  s_coarse [n_coarse^3], fresh [n^3] (caller's N(0,1) draws), out
+ * [n^3]: device arrays of the plan's precision, caller-owned; out may not alias
+ * the inputs.  Uses the plan's workspace (call between, not during, forward /
+ * adjoint calls on the stream).  Errors: PM_ERR_INVALID_ARG, PM_ERR_CUDA. */
+pm_status pm_refine_noise(pm_plan *plan, const void *s_coarse, int32_t n_coarse, const void *fresh, void *out,
+                          pm_stream_t stream);
+
+/* Coarse mesh of (n / factor)^3 cells from a mesh of n^3 cells: the sum
+ * (mean = 0, e.g. galaxy counts) or the mean (mean = 1, e.g. the survey
+ * response R) of each factor^3 block, added in FP64.  n and factor powers of
+ * two, factor <= n <= 1024; in [n^3], out [(n/factor)^3] device arrays of the
+ * given precision, caller-owned.  Errors: PM_ERR_INVALID_ARG, PM_ERR_CUDA. */
+pm_status pm_coarsen(int32_t n, int32_t factor, int32_t precision, int32_t mean, const void *in, void *out,
+                     pm_stream_t stream);
+
 /* ---- kernel timing (no counterpart in the paper; diagnostics) ----------
  * pm_profile(plan, 1, capacity) creates 2*capacity CUDA events and from then
  * on brackets every launch of the profiled kernel classes on its stream

@@ -67,6 +67,8 @@ SIGNATURES = {
     "pm_force": (_I32, [_P, _P, _P, _P, _P]),
     "pm_evolve": (_I32, [_P, _P, _P, _P, _P]),
     "pm_expected_counts": (_I32, [_P, _P, _P, _P, _P]),
+    "pm_refine_noise": (_I32, [_P, _P, _I32, _P, _P, _P]),
+    "pm_coarsen": (_I32, [_I32, _I32, _I32, _I32, _P, _P, _P]),
     "pm_profile": (_I32, [_P, _I32, _I32]),
     "pm_profile_read": (_I32, [_P, _I32, _DP, _I64P, _DP]),
     "pm_rom_fourier_counts": (_I32, [_P, _I64P]),

@@ -213,6 +213,27 @@ def pm_expected_counts(plan, s, R, out=None, stream=None):
     return out
 
 
+def pm_refine_noise(plan, s_coarse, fresh, out=None, stream=None):
+    """White noise on the plan's mesh keeping the coarse field's modes (annealing)."""
+    n_c = int(round(s_coarse.numel() ** (1.0 / 3.0)))
+    out = plan.empty() if out is None else out
+    L.check(L.load().pm_refine_noise(plan.handle, _ptr(s_coarse, plan.dtype, n_c ** 3, "s_coarse"), n_c,
+                                     plan.mesh(fresh, "fresh"), plan.mesh(out, "out"), _stream(stream)),
+            "pm_refine_noise")
+    return out
+
+
+def pm_coarsen(x, factor, mean=False, stream=None):
+    """Block sums (mean=False) or means of factor^3 cells of a cubic CUDA mesh."""
+    n = x.shape[0]
+    nc = n // factor
+    out = torch.empty((nc, nc, nc), dtype=x.dtype, device=x.device)
+    prec = L.PM_PREC_F32 if x.dtype == torch.float32 else L.PM_PREC_F64
+    L.check(L.load().pm_coarsen(n, factor, prec, 1 if mean else 0, _ptr(x, x.dtype, n ** 3, "x"),
+                                _ptr(out, x.dtype, nc ** 3, "out"), _stream(stream)), "pm_coarsen")
+    return out
+
+
 PROFILE_CLASSES = {"kdk": 0, "z_r2c": 1, "col": 2, "x_fused": 3, "z_c2r": 4, "adj_paint": 5,
                    "adj_gather": 6, "loss": 7}
 

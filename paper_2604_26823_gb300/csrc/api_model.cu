@@ -278,6 +278,44 @@ pm_status pm_expected_counts(pm_plan *plan, const void *s, const void *R, void *
   PM_BOTH(E.expected_counts((const T *)s, (const T *)R, (T *)out));
 }
 
+pm_status pm_refine_noise(pm_plan *plan, const void *s_coarse, int32_t n_coarse, const void *fresh, void *out,
+                          pm_stream_t stream) {
+  if (!plan || !s_coarse || !fresh || !out) {
+    pm::set_error("NULL plan / s_coarse / fresh / out");
+    return PM_ERR_INVALID_ARG;
+  }
+  const int n = plan->f32 ? plan->f32->n : plan->f64->n;
+  if (n_coarse < 2 || n_coarse >= n || (n_coarse & (n_coarse - 1))) {
+    pm::set_error("n_coarse must be a power of two in [2, n)");
+    return PM_ERR_INVALID_ARG;
+  }
+  PM_BOTH(E.refine_noise((const T *)s_coarse, n_coarse, (const T *)fresh, (T *)out));
+}
+
+pm_status pm_coarsen(int32_t n, int32_t factor, int32_t precision, int32_t mean, const void *in, void *out,
+                     pm_stream_t stream) {
+  if (!in || !out || n < 2 || n > 1024 || (n & (n - 1)) || factor < 2 || factor > n || (factor & (factor - 1)) ||
+      (precision != PM_PREC_F32 && precision != PM_PREC_F64) || (mean != 0 && mean != 1)) {
+    pm::set_error("invalid coarsen arguments");
+    return PM_ERR_INVALID_ARG;
+  }
+  int logn = 0, logr = 0;
+  while ((1 << logn) < n) ++logn;
+  while ((1 << logr) < factor) ++logr;
+  const int logc = logn - logr;
+  const int64_t mc = (int64_t)1 << (3 * logc);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  ::pm::note_launch();
+  if (precision == PM_PREC_F32)
+    pm::pw::k_block_reduce<float><<<pm::grid_for(mc, 256), 256, 0, s>>>((const float *)in, logc, logr, mean != 0,
+                                                                       (float *)out);
+  else
+    pm::pw::k_block_reduce<double><<<pm::grid_for(mc, 256), 256, 0, s>>>((const double *)in, logc, logr,
+                                                                        mean != 0, (double *)out);
+  PM_LAUNCH_CHECK();
+  return PM_OK;
+}
+
 pm_status pm_profile(pm_plan *plan, int32_t enable, int32_t capacity) {
   if (!plan || (enable && capacity < 1)) {
     pm::set_error("invalid profiler arguments");

@@ -869,6 +869,33 @@ template <typename T> struct Engine {
     return PM_OK;
   }
 
+  // ---- resolution transfer of the white noise (annealing) ----
+  // s_fine(k) = r^{3/2} s_c(k) on the coarse modes with every |n_i| < n_c / 2,
+  // fresh(k) on all other modes (r = n / n_c): the fine field keeps the coarse
+  // field's linear density (the IC amplitude scales as Delta^{-3/2}) and stays
+  // unit white noise.  The coarse spectrum comes from the fine FFT of the
+  // zero-stuffed coarse field; psi (rebuilt by every forward) is the scratch.
+  pm_status refine_noise(const T *sc, int n_c, const T *fresh, T *out) {
+    int logc = 0;
+    while ((1 << logc) < n_c) ++logc;
+    const int logr = logn - logc;
+    ::pm::note_launch();
+    pw::k_zero_stuff<T><<<grid_for(M, 256), 256, 0, st>>>(sc, logn, logr, psi);
+    PM_LAUNCH_CHECK();
+    PM_CUDA_TRY(cudaMemcpyAsync(psi + M, fresh, M * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    PM_TRY(r2c_real(psi, 2, slot(0)));
+    PM_TRY(ypass(slot(0), 2, -1));
+    const double r3 = std::ldexp(1.0, 3 * logr);
+    fft::MultDesc m[2] = {md(std::sqrt(r3) * inv_n3(), -1, -1, fft::M_INCUBE),
+                          md(inv_n3(), -1, -1, fft::M_OUTCUBE)};
+    m[0].cube = m[1].cube = n_c / 2;
+    int ins[2] = {0, 1};
+    PM_TRY(xMto1(ins, 0, m, 2));
+    PM_TRY(ypass(slot(0), 1, +1));
+    PM_TRY((c2r<1>(0, 1, OutPlanar<T>{out, n})));
+    return PM_OK;
+  }
+
   // ---- probes ----
   pm_status linear_field(const T *s, T *out) {
     PM_TRY(r2c_real(s, 1, slot(0)));

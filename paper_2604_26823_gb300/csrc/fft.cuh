@@ -143,13 +143,15 @@ __device__ __forceinline__ void smem_fft(C *buf, const C *__restrict__ tw, int t
 }
 
 // ---- spectral multipliers -----------------------------------------------
-enum : int { M_INVK2 = 1, M_AMP = 2, M_CONJ = 4 };
+enum : int { M_INVK2 = 1, M_AMP = 2, M_CONJ = 4, M_INCUBE = 8, M_OUTCUBE = 16 };
 
 // h(k) = scale * [A(k)] * [1/k^2 (0 at k = 0)] * D_d1(k) * D_d2(k), with
 // D_i = i k_i (0 at the Nyquist index of axis i); conjugated on M_CONJ.
+// M_INCUBE keeps only the modes with every |n_i| < cube (integer wave
+// numbers), M_OUTCUBE only the others.
 struct MultDesc {
   double scale;
-  int d1, d2, flags, pad;
+  int d1, d2, flags, cube;
 };
 struct MultSet {
   MultDesc m[9];
@@ -159,6 +161,7 @@ struct MultSet {
 template <typename T> struct ModeK {
   T k[3];   // k_i, zero at that axis' Nyquist index
   T ik2;    // 1/|k|^2, zero at k = 0
+  int amax; // max_i |n_i|
 };
 
 template <typename T>
@@ -173,6 +176,7 @@ __device__ __forceinline__ ModeK<T> mode_k(int ix, int iy, int iz, int n, T kf) 
   m.k[2] = (iz == h) ? T(0) : kf * (T)nz;
   const int n2 = nx * nx + ny * ny + nz * nz;
   m.ik2 = n2 > 0 ? T(1) / (kf * kf * (T)n2) : T(0);
+  m.amax = max(abs(nx), max(abs(ny), nz));
   return m;
 }
 
@@ -181,7 +185,7 @@ __device__ __forceinline__ ModeK<T> mode_k(int ix, int iy, int iz, int n, T kf) 
 // element (same arithmetic as mode_k).
 template <typename T> struct ColMode {
   T ky, kz, kf;
-  int nyz2, h, n;
+  int nyz2, ayz, h, n;
   __device__ __forceinline__ void init(int iy, int iz, int n_, T kf_) {
     n = n_;
     h = n >> 1;
@@ -190,6 +194,7 @@ template <typename T> struct ColMode {
     ky = (iy == h) ? T(0) : kf * (T)ny;
     kz = (iz == h) ? T(0) : kf * (T)iz;
     nyz2 = ny * ny + iz * iz;
+    ayz = max(abs(ny), iz);
   }
   __device__ __forceinline__ ModeK<T> at(int ix) const {
     ModeK<T> m;
@@ -199,6 +204,7 @@ template <typename T> struct ColMode {
     m.k[2] = kz;
     const int n2 = nx * nx + nyz2;
     m.ik2 = n2 > 0 ? T(1) / (kf * kf * (T)n2) : T(0);
+    m.amax = max(abs(nx), ayz);
     return m;
   }
 };
@@ -208,6 +214,10 @@ __device__ __forceinline__ C apply_mult(const MultDesc &d, C x, const ModeK<T> &
   T f = (T)d.scale;
   if (d.flags & M_AMP) f *= amp;
   if (d.flags & M_INVK2) f *= mk.ik2;
+  if (d.flags & (M_INCUBE | M_OUTCUBE)) {
+    const bool in = mk.amax < d.cube;
+    if ((d.flags & M_INCUBE) ? !in : in) f = T(0);
+  }
   int nd = 0;
   if (d.d1 >= 0) {
     f *= mk.k[d.d1];

@@ -220,6 +220,42 @@ template <typename T> __global__ void k_scale(const T *__restrict__ x, T a, T *_
   if (i < n) out[i] = a * x[i];
 }
 
+// Zero-stuffing onto the fine mesh (2^logn per side) of a coarse field with
+// 2^(logn - logr) cells per side: out(x) = s_c(x / r) where r divides every
+// coordinate of x, 0 elsewhere.  Its fine DFT is the coarse DFT repeated over
+// k (mod coarse size), so the fine FFT of it yields the coarse modes.
+template <typename T>
+__global__ void k_zero_stuff(const T *__restrict__ sc, int logn, int logr, T *__restrict__ out) {
+  const int64_t m = (int64_t)1 << (3 * logn);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int mask = (1 << logn) - 1, rmask = (1 << logr) - 1, lc = logn - logr;
+  const int x = (int)(i >> (2 * logn)), y = (int)(i >> logn) & mask, z = (int)i & mask;
+  T v = T(0);
+  if (((x | y | z) & rmask) == 0)
+    v = sc[((int64_t)(x >> logr) << (2 * lc)) | ((int64_t)(y >> logr) << lc) | (int64_t)(z >> logr)];
+  out[i] = v;
+}
+
+// Block sums (or means) of r^3 fine cells into a coarse mesh of 2^logc cells
+// per side: one thread per coarse cell, children added in lattice order in FP64.
+template <typename T>
+__global__ void k_block_reduce(const T *__restrict__ in, int logc, int logr, bool mean, T *__restrict__ out) {
+  const int64_t mc = (int64_t)1 << (3 * logc);
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= mc) return;
+  const int cmask = (1 << logc) - 1, r = 1 << logr, logn = logc + logr;
+  const int cx = (int)(j >> (2 * logc)), cy = (int)(j >> logc) & cmask, cz = (int)j & cmask;
+  double acc = 0.0;
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < r; ++b) {
+      const int64_t row = ((int64_t)((cx << logr) + a) << (2 * logn)) | ((int64_t)((cy << logr) + b) << logn);
+      for (int c = 0; c < r; ++c) acc += (double)in[row | (int64_t)((cz << logr) + c)];
+    }
+  if (mean) acc /= (double)((int64_t)r * r * r);
+  out[j] = (T)acc;
+}
+
 // out = y + a * x
 template <typename T>
 __global__ void k_axpy(const T *__restrict__ x, const T *__restrict__ y, double a, T *__restrict__ out, int64_t n) {

@@ -101,6 +101,50 @@ def reconstruct(plan, s0, data, R, iters, m=10, eps_max=1.0, c1=1e-4, max_halvin
     return s, f, info
 
 
+def anneal(cfg, lnk, lnp, s0_coarse, data, R, factor, iters_coarse, iters_fine, fresh, rom_every_coarse=5,
+           rom_every_fine=20, targets_for=None, seed=6, trace=None):
+    """Annealed reconstruction (Sec. 3, opening): ``iters_coarse`` iterations at
+    n / factor cells per side (same box; counts summed and R averaged over each
+    factor^3 block by ``pm_coarsen``; nbar_cell scaled by factor^3), then the
+    coarse result carried to the fine mesh by ``pm_refine_noise`` (coarse
+    modes kept, ``fresh`` on the others) and ``iters_fine`` iterations there.
+
+    cfg: the fine ``api.Config``; s0_coarse [n_c^3], data / R / fresh [n^3]:
+    device tensors of cfg's dtype.  targets_for(plan, R)(it) -> ROM targets
+    as ``reconstruct`` takes them (needed when a rom_every is > 0).
+    Returns (s, loss, info) with per-stage info and wall times."""
+    import dataclasses
+    nc = cfg.n // factor
+    cfg_c = dataclasses.replace(cfg, n=nc, nbar_cell=cfg.nbar_cell * factor ** 3)
+    data_c = api.pm_coarsen(data, factor)
+    R_c = api.pm_coarsen(R, factor, mean=True)
+    info = {}
+    plan_c = api.Plan(cfg_c, lnk, lnp)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tg = targets_for(plan_c, R_c) if targets_for and rom_every_coarse else None
+        s_c, f_c, info["coarse"] = reconstruct(plan_c, s0_coarse, data_c, R_c, iters_coarse, rom_every=rom_every_coarse,
+                                               rom_targets=tg, seed=seed, trace=trace)
+        torch.cuda.synchronize()
+        info["coarse"]["seconds"] = time.perf_counter() - t0
+        info["coarse"]["final_loss"] = f_c
+    finally:
+        plan_c.close()
+    plan = api.Plan(cfg, lnk, lnp)
+    try:
+        t0 = time.perf_counter()
+        s1 = api.pm_refine_noise(plan, s_c, fresh)
+        tg = targets_for(plan, R) if targets_for and rom_every_fine else None
+        s, f, info["fine"] = reconstruct(plan, s1, data, R, iters_fine, rom_every=rom_every_fine, rom_targets=tg,
+                                         seed=seed, trace=trace)
+        torch.cuda.synchronize()
+        info["fine"]["seconds"] = time.perf_counter() - t0
+    finally:
+        plan.close()
+    return s, f, info
+
+
 def masked_mock(n, box, n_steps=10, nbar=1e-3, seed_truth=1, seed_counts=3, seed_holes=4, lnk=None, lnp=None):
     """Masked Poisson mock of the benchmark workload: selection R (40 deg cone,
     radial n(r), angular holes), s_true, the mean-density normalisation
@@ -162,36 +206,54 @@ def _main():
     ap.add_argument("--box", type=float, default=500.0)
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--precision", choices=["f32", "f64", "both"], default="both")
+    ap.add_argument("--steps", type=int, default=10, help="leapfrog steps (the paper's run: 18, da = 0.05)")
+    ap.add_argument("--anneal", type=int, default=0,
+                    help="coarsening factor of a first, low-resolution stage (0: none; the paper: 4 cMpc/h cells)")
+    ap.add_argument("--coarse-iters", type=int, default=250)
     args = ap.parse_args()
     from . import build
     build.build()
     lnk, lnp = api.pm_linear_power_table()
-    R, s_true, counts, nbar_cell = masked_mock(args.n, args.box, lnk=lnk, lnp=lnp)
+    R, s_true, counts, nbar_cell = masked_mock(args.n, args.box, n_steps=args.steps, lnk=lnk, lnp=lnp)
     s0 = inputs.white_noise(args.n, 2)
     out = {"workload": f"masked-recon-{args.n}", "n": args.n, "box": args.box, "iters": args.iters,
-           "galaxies": float(counts.sum()), "nbar_cell": nbar_cell}
+           "steps": args.steps, "galaxies": float(counts.sum()), "nbar_cell": nbar_cell}
+    if args.anneal:
+        out["workload"] = f"annealed-masked-recon-{args.n // args.anneal}-{args.n}"
+        out["coarse_iters"] = args.coarse_iters
     precs = ["f32", "f64"] if args.precision == "both" else [args.precision]
     for prec in precs:
         dt = torch.float32 if prec == "f32" else torch.float64
         dev = lambda x: torch.as_tensor(np.asarray(x)).to(device="cuda", dtype=dt)
-        plan = api.Plan(mock_config(args.n, args.box, nbar_cell, prec), lnk, lnp)
+        cfg = mock_config(args.n, args.box, nbar_cell, prec, n_steps=args.steps)
         Rd, cd = dev(R), dev(counts)
-        nreal = api.pm_count_positive(plan, Rd)
-        fcounts = api.pm_rom_fourier_counts(plan)
-        targets = lambda it: (dev(inputs.sorted_normal_targets(nreal, 7 + it)),
-                              dev(inputs.sorted_normal_targets_per_bin(fcounts, 7 + it)))
+
+        def targets_for(plan, Rm):
+            nreal = api.pm_count_positive(plan, Rm)
+            fcounts = api.pm_rom_fourier_counts(plan)
+            return lambda it: (dev(inputs.sorted_normal_targets(nreal, 7 + it)),
+                               dev(inputs.sorted_normal_targets_per_bin(fcounts, 7 + it)))
+
         trace = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s, f, info = reconstruct(plan, dev(s0), cd, Rd, args.iters, rom_targets=targets, trace=trace)
+        if args.anneal:
+            nc = args.n // args.anneal
+            s, f, info = anneal(cfg, lnk, lnp, dev(inputs.white_noise(nc, 2)), cd, Rd, args.anneal,
+                                args.coarse_iters, args.iters, dev(inputs.white_noise(args.n, 8)),
+                                targets_for=targets_for, trace=trace)
+        else:
+            plan = api.Plan(cfg, lnk, lnp)
+            s, f, info = reconstruct(plan, dev(s0), cd, Rd, args.iters, rom_targets=targets_for(plan, Rd),
+                                     trace=trace)
+            plan.close()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         k, r = cross_correlation(s.double().cpu().numpy(), s_true, args.box)
         out[prec] = {"final_loss": f, "seconds": wall, "iters_per_s": args.iters / wall, **info,
                      "loss_trace": [(i, l) for i, l in trace if i % max(1, args.iters // 10) == 0],
                      "r_k": {"k": [round(x, 4) for x in k[:8]], "r": [round(x, 4) for x in r[:8]]}}
-        plan.close()
-        del plan, s
+        del s
         torch.cuda.empty_cache()
     if "f32" in out and "f64" in out:
         out["final_loss_rel_diff"] = abs(out["f32"]["final_loss"] - out["f64"]["final_loss"]) / abs(
