@@ -36,12 +36,18 @@ class LineSearchError(RuntimeError):
 
 
 def reconstruct(plan, s0, data, R, iters, m=10, eps_max=1.0, c1=1e-4, max_halvings=30, rom_every=20,
-                rom_targets=None, seed=6, trace=None):
+                rom_targets=None, seed=6, trace=None, project=True, checkpoint_every=0, on_checkpoint=None):
     """Run ``iters`` iterations from s0 (not modified).
 
     rom_targets(it) -> (targets_real, targets_fourier), device tensors of the
     plan's dtype, sorted descending (required when rom_every > 0).
     trace: optional list receiving (iteration, loss) after every iteration.
+    project=False with rom_every=0 is the vanilla L-BFGS of the ablation
+    (Appendix B): no projection of the trial points, no rank-order matching.
+    checkpoint_every > 0: after every that many iterations (after the
+    rank-order matching when both fall on the iteration) ``on_checkpoint``
+    is called with (iteration, s, loss, likelihood term); s is the driver's
+    own buffer, to be copied if kept.
     Returns (s, loss, info)."""
     if rom_every and rom_targets is None:
         raise ValueError("rom_every > 0 needs rom_targets")
@@ -64,9 +70,10 @@ def reconstruct(plan, s0, data, R, iters, m=10, eps_max=1.0, c1=1e-4, max_halvin
             slope = gd / dn
             for t in range(max_halvings + 1):
                 api.pm_axpy(eps / dn, d, s, out=trial)
-                info["resets_of_values"] += api.project_rank_match(plan, trial, L.PM_PROJECT, seed=seed,
-                                                                   counter=counter)
-                counter += 1
+                if project:
+                    info["resets_of_values"] += api.project_rank_match(plan, trial, L.PM_PROJECT, seed=seed,
+                                                                       counter=counter)
+                    counter += 1
                 ft, _ = api.pm_adjoint(plan, trial, data, R, grad_out=gt)
                 info["evals"] += 1
                 if math.isfinite(ft) and ft <= f + c1 * eps * slope:
@@ -95,6 +102,8 @@ def reconstruct(plan, s0, data, R, iters, m=10, eps_max=1.0, c1=1e-4, max_halvin
             info["evals"] += 1
             info["rom"] += 1
             api.lbfgs_reset(st)
+        if checkpoint_every and it % checkpoint_every == 0 and on_checkpoint is not None:
+            on_checkpoint(it, s, f, api.pm_last_terms(plan)[0])
         if trace is not None:
             trace.append((it, f))
     st.close()
