@@ -190,6 +190,50 @@ pm_status pm_expected_counts(pm_plan *plan, const void *s, const void *R, void *
 pm_status pm_refine_noise(pm_plan *plan, const void *s_coarse, int32_t n_coarse, const void *fresh, void *out,
                           pm_stream_t stream);
 
+/* ---- analysis of fields (Sec. 3.2: r_c(k); Sec. 3.3: the T-web) ---------- */
+
+/* Binned power spectra of one or two real fields on the plan's mesh (device
+ * arrays [n^3] of the plan's precision; b may be NULL): with the DFT
+ * X(k) = sum_x x e^{-ikx}, P(k) = (V / n^6) sum |X|^2 over the modes of a bin
+ * divided by their number (cross spectrum: Re(A conj B)), V = box^3; the mode
+ * of integer wave vector m, |k| = (2 pi / box) |m|, falls in bin
+ * floor((|k| - k_min) / dk), dk = (k_max - k_min) / n_bins, when that lies in
+ * [0, n_bins).  Host outputs of n_bins doubles: p_aa, counts (required), p_bb,
+ * p_ab (nullable; 0 when b is NULL); empty bins give NaN.  r_c = p_ab /
+ * sqrt(p_aa p_bb).  Uses the plan's workspace; synchronises the stream.  Bin
+ * sums are FP64 atomics, so the last bits may differ between calls.  Errors:
+ * PM_ERR_INVALID_ARG (n_bins outside [1, 1024], k_max <= k_min), PM_ERR_CUDA. */
+pm_status pm_power_spectra(pm_plan *plan, const void *a, const void *b, int32_t n_bins, double k_min, double k_max,
+                           double *p_aa, double *p_bb, double *p_ab, double *counts, pm_stream_t stream);
+
+/* Gaussian smoothing out = IFFT[exp(-|k|^2 r_sm^2 / 2) FFT(in)] (r_sm in Mpc/h,
+ * >= 0), device arrays [n^3] of the plan's precision (in-place allowed). */
+pm_status pm_smooth(pm_plan *plan, const void *in, double r_sm, void *out, pm_stream_t stream);
+
+/* T-web classification of a density contrast field (device [n^3], plan's
+ * precision): psi_ij(k) = k_i k_j / |k|^2 exp(-|k|^2 r_sm^2 / 2) delta(k) (k_i = 0 at
+ * axis i's Nyquist index, psi(0) = 0), per cell eigenvalues
+ * lambda_1 <= lambda_2 <= lambda_3 (FP64 closed form of the cubic) and unit
+ * eigenvectors; labels[c] = number of eigenvalues above lambda_th (0 void,
+ * 1 sheet, 2 filament, 3 knot; the paper: r_sm = 2 Mpc/h, lambda_th = 0.16).
+ * Outputs (device, caller-owned): labels int32 [n^3] (required), eig [3][n^3]
+ * and evec [3 (which) x 3 (component)][n^3] in the plan's precision (nullable).
+ * Uses the plan's workspace. */
+pm_status pm_tweb(pm_plan *plan, const void *delta, double r_sm, double lambda_th, int32_t *labels, void *eig,
+                  void *evec, pm_stream_t stream);
+
+/* Cosine similarity |e_i,a . e_i,b| (i = 1, 2, 3) of two eigenvector fields in
+ * pm_tweb's layout; out [3][n_cells]; device arrays of the given precision. */
+pm_status pm_eigvec_cosines(int64_t n_cells, int32_t precision, const void *va, const void *vb, void *out,
+                            pm_stream_t stream);
+
+/* Confusion matrix of two T-web labelings over the cells with R > 0 (all
+ * cells when R is NULL; R in the given precision): counts_out (device int64
+ * [16], overwritten) [4 * truth + reconstructed]; labels outside 0..3 are not
+ * counted. */
+pm_status pm_confusion(int64_t n_cells, int32_t precision, const int32_t *labels_truth, const int32_t *labels_rec,
+                       const void *R, int64_t *counts_out, pm_stream_t stream);
+
 /* Coarse mesh of (n / factor)^3 cells from a mesh of n^3 cells: the sum
  * (mean = 0, e.g. galaxy counts) or the mean (mean = 1, e.g. the survey
  * response R) of each factor^3 block, added in FP64.  n and factor powers of

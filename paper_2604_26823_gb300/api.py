@@ -234,6 +234,67 @@ def pm_coarsen(x, factor, mean=False, stream=None):
     return out
 
 
+def pm_power_spectra(plan, a, b=None, n_bins=16, k_min=None, k_max=None, stream=None):
+    """(k centres, P_aa, P_bb, P_ab, counts, r_c) as numpy arrays; default bins
+    linear from the fundamental to the Nyquist wave number."""
+    kf = 2 * np.pi / plan.config.box
+    k_min = kf if k_min is None else k_min
+    k_max = kf * plan.config.n / 2 if k_max is None else k_max
+    out = [np.zeros(n_bins) for _ in range(4)]
+    L.check(L.load().pm_power_spectra(plan.handle, plan.mesh(a, "a"), plan.mesh(b, "b"), n_bins, k_min, k_max,
+                                      *[o.ctypes.data_as(L._DP) for o in out], _stream(stream)),
+            "pm_power_spectra")
+    paa, pbb, pab, cnt = out
+    edges = np.linspace(k_min, k_max, n_bins + 1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = pab / np.sqrt(paa * pbb)
+    return 0.5 * (edges[1:] + edges[:-1]), paa, pbb, pab, cnt, r
+
+
+def pm_smooth(plan, x, r_sm, out=None, stream=None):
+    out = plan.empty() if out is None else out
+    L.check(L.load().pm_smooth(plan.handle, plan.mesh(x, "x"), float(r_sm), plan.mesh(out, "out"), _stream(stream)),
+            "pm_smooth")
+    return out
+
+
+def pm_tweb(plan, delta, r_sm=2.0, lambda_th=0.16, want_eig=True, want_evec=True, stream=None):
+    """(labels int32 [n,n,n], eigenvalues [3,n,n,n] or None, eigenvectors
+    [3 (which), 3 (component), n, n, n] or None)."""
+    n = plan.config.n
+    labels = torch.empty((n, n, n), dtype=torch.int32, device="cuda")
+    eig = torch.empty((3, n, n, n), dtype=plan.dtype, device="cuda") if want_eig else None
+    evec = torch.empty((3, 3, n, n, n), dtype=plan.dtype, device="cuda") if want_evec else None
+    L.check(L.load().pm_tweb(plan.handle, plan.mesh(delta, "delta"), float(r_sm), float(lambda_th),
+                             _ptr(labels, torch.int32, n ** 3, "labels"),
+                             _ptr(eig, plan.dtype, 3 * n ** 3, "eig"), _ptr(evec, plan.dtype, 9 * n ** 3, "evec"),
+                             _stream(stream)), "pm_tweb")
+    return labels, eig, evec
+
+
+def pm_eigvec_cosines(va, vb, stream=None):
+    """|e_i,a . e_i,b| per cell, [3, ...] for eigenvector fields [3, 3, ...]."""
+    ncell = va.numel() // 9
+    out = torch.empty((3,) + tuple(va.shape[2:]), dtype=va.dtype, device=va.device)
+    prec = L.PM_PREC_F32 if va.dtype == torch.float32 else L.PM_PREC_F64
+    L.check(L.load().pm_eigvec_cosines(ncell, prec, _ptr(va, va.dtype, 9 * ncell, "va"),
+                                       _ptr(vb, va.dtype, 9 * ncell, "vb"), _ptr(out, va.dtype, 3 * ncell, "out"),
+                                       _stream(stream)), "pm_eigvec_cosines")
+    return out
+
+
+def pm_confusion(labels_truth, labels_rec, R=None, stream=None):
+    """4 x 4 numpy counts [truth, reconstructed] over the cells with R > 0."""
+    ncell = labels_truth.numel()
+    out = torch.empty(16, dtype=torch.int64, device=labels_truth.device)
+    prec = L.PM_PREC_F64 if (R is not None and R.dtype == torch.float64) else L.PM_PREC_F32
+    L.check(L.load().pm_confusion(ncell, prec, _ptr(labels_truth, torch.int32, ncell, "labels_truth"),
+                                  _ptr(labels_rec, torch.int32, ncell, "labels_rec"),
+                                  _ptr(R, R.dtype, ncell, "R") if R is not None else None,
+                                  _ptr(out, torch.int64, 16, "counts"), _stream(stream)), "pm_confusion")
+    return out.cpu().numpy().reshape(4, 4)
+
+
 PROFILE_CLASSES = {"kdk": 0, "z_r2c": 1, "col": 2, "x_fused": 3, "z_c2r": 4, "adj_paint": 5,
                    "adj_gather": 6, "loss": 7}
 

@@ -1,7 +1,9 @@
 // C ABI of the particle-mesh model: plan lifecycle, forward, adjoint,
 // stage probes and the host-side coefficient helpers.
+#include <algorithm>
 #include <cmath>
 #include <new>
+#include <vector>
 #include <string>
 
 #include "api_internal.h"
@@ -312,6 +314,91 @@ pm_status pm_coarsen(int32_t n, int32_t factor, int32_t precision, int32_t mean,
   else
     pm::pw::k_block_reduce<double><<<pm::grid_for(mc, 256), 256, 0, s>>>((const double *)in, logc, logr,
                                                                         mean != 0, (double *)out);
+  PM_LAUNCH_CHECK();
+  return PM_OK;
+}
+
+pm_status pm_power_spectra(pm_plan *plan, const void *a, const void *b, int32_t n_bins, double k_min, double k_max,
+                           double *p_aa, double *p_bb, double *p_ab, double *counts, pm_stream_t stream) {
+  if (!plan || !a || !p_aa || !counts || n_bins < 1 || n_bins > 1024 || !std::isfinite(k_min) ||
+      !std::isfinite(k_max) || !(k_max > k_min)) {
+    pm::set_error("invalid power spectrum arguments (n_bins in [1, 1024], k_max > k_min, outputs)");
+    return PM_ERR_INVALID_ARG;
+  }
+  std::vector<double> h(4 * (size_t)n_bins);
+  pm_status s;
+  if (plan->f32) {
+    auto &E = *plan->f32;
+    E.st = reinterpret_cast<cudaStream_t>(stream);
+    s = E.power_spectra((const float *)a, (const float *)b, n_bins, k_min, k_max, h.data());
+  } else {
+    auto &E = *plan->f64;
+    E.st = reinterpret_cast<cudaStream_t>(stream);
+    s = E.power_spectra((const double *)a, (const double *)b, n_bins, k_min, k_max, h.data());
+  }
+  if (s != PM_OK) return s;
+  for (int j = 0; j < n_bins; ++j) {
+    p_aa[j] = h[j];
+    if (p_bb) p_bb[j] = h[n_bins + j];
+    if (p_ab) p_ab[j] = h[2 * n_bins + j];
+    counts[j] = h[3 * n_bins + j];
+  }
+  return PM_OK;
+}
+
+pm_status pm_smooth(pm_plan *plan, const void *in, double r_sm, void *out, pm_stream_t stream) {
+  if (!plan || !in || !out || !(r_sm >= 0) || !std::isfinite(r_sm)) {
+    pm::set_error("NULL in / out or invalid smoothing radius");
+    return PM_ERR_INVALID_ARG;
+  }
+  PM_BOTH(E.smooth((const T *)in, r_sm, (T *)out));
+}
+
+pm_status pm_tweb(pm_plan *plan, const void *delta, double r_sm, double lambda_th, int32_t *labels, void *eig,
+                  void *evec, pm_stream_t stream) {
+  if (!plan || !delta || !labels || !(r_sm >= 0) || !std::isfinite(r_sm) || !std::isfinite(lambda_th)) {
+    pm::set_error("NULL delta / labels or invalid smoothing radius / threshold");
+    return PM_ERR_INVALID_ARG;
+  }
+  PM_BOTH(E.tweb((const T *)delta, r_sm, lambda_th, (int *)labels, (T *)eig, (T *)evec));
+}
+
+pm_status pm_eigvec_cosines(int64_t n_cells, int32_t precision, const void *va, const void *vb, void *out,
+                            pm_stream_t stream) {
+  if (n_cells < 0 || !va || !vb || !out || (precision != PM_PREC_F32 && precision != PM_PREC_F64)) {
+    pm::set_error("invalid eigenvector cosine arguments");
+    return PM_ERR_INVALID_ARG;
+  }
+  if (n_cells == 0) return PM_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  ::pm::note_launch();
+  if (precision == PM_PREC_F32)
+    pm::an::k_eig_cosines<float><<<pm::grid_for(n_cells, 256), 256, 0, s>>>((const float *)va, (const float *)vb,
+                                                                            n_cells, (float *)out);
+  else
+    pm::an::k_eig_cosines<double><<<pm::grid_for(n_cells, 256), 256, 0, s>>>(
+        (const double *)va, (const double *)vb, n_cells, (double *)out);
+  PM_LAUNCH_CHECK();
+  return PM_OK;
+}
+
+pm_status pm_confusion(int64_t n_cells, int32_t precision, const int32_t *labels_truth, const int32_t *labels_rec,
+                       const void *R, int64_t *counts_out, pm_stream_t stream) {
+  if (n_cells < 0 || !labels_truth || !labels_rec || !counts_out ||
+      (precision != PM_PREC_F32 && precision != PM_PREC_F64)) {
+    pm::set_error("invalid confusion arguments");
+    return PM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  PM_CUDA_TRY(cudaMemsetAsync(counts_out, 0, 16 * sizeof(int64_t), s));
+  if (n_cells == 0) return PM_OK;
+  const int grid = (int)std::min<int64_t>(pm::grid_for(n_cells, 256), 152 * 8);
+  auto *o = reinterpret_cast<unsigned long long *>(counts_out);
+  ::pm::note_launch();
+  if (precision == PM_PREC_F32)
+    pm::an::k_confusion<float><<<grid, 256, 0, s>>>(labels_truth, labels_rec, (const float *)R, n_cells, o);
+  else
+    pm::an::k_confusion<double><<<grid, 256, 0, s>>>(labels_truth, labels_rec, (const double *)R, n_cells, o);
   PM_LAUNCH_CHECK();
   return PM_OK;
 }

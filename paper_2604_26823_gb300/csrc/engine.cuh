@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/mujica_pm.h"
+#include "analysis.cuh"
 #include "common.cuh"
 #include "fft.cuh"
 #include "host_cosmo.h"
@@ -893,6 +894,70 @@ template <typename T> struct Engine {
     PM_TRY(xMto1(ins, 0, m, 2));
     PM_TRY(ypass(slot(0), 1, +1));
     PM_TRY((c2r<1>(0, 1, OutPlanar<T>{out, n})));
+    return PM_OK;
+  }
+
+  // ---- analysis of fields (Sec. 3.2, 3.3) ----
+  // Binned P_aa, P_bb, P_ab and mode counts (host[4][nbins]); b may be null.
+  // P = (V / n^6) sum w |X|^2 / sum w over the bin's half-spectrum modes.
+  pm_status power_spectra(const T *a, const T *b, int nbins, double kmin, double kmax, double *host) {
+    double *bins = reinterpret_cast<double *>(fx);  // the paint meshes are free between model calls
+    PM_CUDA_TRY(cudaMemsetAsync(bins, 0, 4 * (size_t)nbins * sizeof(double), st));
+    PM_TRY(r2c_real(a, 1, slot(0)));
+    if (b) PM_TRY(r2c_real(b, 1, slot(1)));
+    PM_TRY(ypass(slot(0), b ? 2 : 1, -1));
+    const double dk = (kmax - kmin) / nbins;
+    PM_DISPATCH_N(n, {
+      using CC = CCfg<T, NN>;
+      auto kern = an::k_x_power<T, NN, CC::B, CC::NT>;
+      const size_t sm = CC::SMEM2 + 4 * (size_t)nbins * sizeof(double);
+      set_smem(kern, sm);
+      ::pm::note_launch();
+      kern<<<(int)(S / n / CC::B), CC::NT, sm, st>>>(slot(0), b ? slot(1) : nullptr, tw, kf, kmin, dk, nbins,
+                                                    bins);
+    });
+    PM_LAUNCH_CHECK();
+    PM_CUDA_TRY(cudaMemcpyAsync(host, bins, 4 * (size_t)nbins * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    const double norm = cfg.box * cfg.box * cfg.box / ((double)M * (double)M);
+    for (int j = 0; j < nbins; ++j) {
+      const double cnt = host[3 * nbins + j];
+      for (int q = 0; q < 3; ++q) host[q * nbins + j] = cnt > 0 ? host[q * nbins + j] * norm / cnt : NAN;
+    }
+    return PM_OK;
+  }
+  // out = IFFT[exp(-|k|^2 r^2 / 2) FFT(in)]
+  pm_status smooth(const T *in, double r, T *out) {
+    PM_TRY(r2c_real(in, 1, slot(0)));
+    PM_TRY(ypass(slot(0), 1, -1));
+    fft::MultDesc m = md(inv_n3(), -1, -1, fft::M_GAUSS);
+    m.gauss = 0.5 * r * r;
+    int o = 0;
+    PM_TRY(x1toM(slot(0), &o, &m, 1));
+    PM_TRY(ypass(slot(0), 1, +1));
+    PM_TRY((c2r<1>(0, 1, OutPlanar<T>{out, n})));
+    return PM_OK;
+  }
+  // T-web: psi_ij = IFFT[k_i k_j / k^2 G(k) FFT(delta)] (into the 2LPT scratch),
+  // then the per-cell eigen-decomposition and label.
+  pm_status tweb(const T *delta, double r, double th, int *labels, T *eig, T *evec) {
+    PM_TRY(r2c_real(delta, 1, slot(0)));
+    PM_TRY(ypass(slot(0), 1, -1));
+    fft::MultDesc m[6];
+    int outs[6];
+    for (int c = 0; c < 6; ++c) {
+      int i, j;
+      pair_of(c, i, j);
+      m[c] = md(-inv_n3(), i, j, fft::M_INVK2 | fft::M_GAUSS);  // -(i k_i)(i k_j) / k^2 G
+      m[c].gauss = 0.5 * r * r;
+      outs[c] = c;
+    }
+    PM_TRY(x1toM(slot(0), outs, m, 6));
+    PM_TRY(ypass(slot(0), 6, +1));
+    PM_TRY((c2r<1>(0, 6, OutPlanar<T>{psi, n})));
+    ::pm::note_launch();
+    an::k_tweb_eigen<T><<<grid_for(M, 256), 256, 0, st>>>(psi, M, th, labels, eig, evec);
+    PM_LAUNCH_CHECK();
     return PM_OK;
   }
 

@@ -143,15 +143,17 @@ __device__ __forceinline__ void smem_fft(C *buf, const C *__restrict__ tw, int t
 }
 
 // ---- spectral multipliers -----------------------------------------------
-enum : int { M_INVK2 = 1, M_AMP = 2, M_CONJ = 4, M_INCUBE = 8, M_OUTCUBE = 16 };
+enum : int { M_INVK2 = 1, M_AMP = 2, M_CONJ = 4, M_INCUBE = 8, M_OUTCUBE = 16, M_GAUSS = 32 };
 
 // h(k) = scale * [A(k)] * [1/k^2 (0 at k = 0)] * D_d1(k) * D_d2(k), with
 // D_i = i k_i (0 at the Nyquist index of axis i); conjugated on M_CONJ.
 // M_INCUBE keeps only the modes with every |n_i| < cube (integer wave
-// numbers), M_OUTCUBE only the others.
+// numbers), M_OUTCUBE only the others; M_GAUSS multiplies by
+// exp(-gauss |k|^2) (gauss = R^2 / 2 for a Gaussian of width R).
 struct MultDesc {
   double scale;
   int d1, d2, flags, cube;
+  double gauss;
 };
 struct MultSet {
   MultDesc m[9];
@@ -161,6 +163,7 @@ struct MultSet {
 template <typename T> struct ModeK {
   T k[3];   // k_i, zero at that axis' Nyquist index
   T ik2;    // 1/|k|^2, zero at k = 0
+  T k2;     // |k|^2 (Nyquist components included)
   int amax; // max_i |n_i|
 };
 
@@ -176,6 +179,7 @@ __device__ __forceinline__ ModeK<T> mode_k(int ix, int iy, int iz, int n, T kf) 
   m.k[2] = (iz == h) ? T(0) : kf * (T)nz;
   const int n2 = nx * nx + ny * ny + nz * nz;
   m.ik2 = n2 > 0 ? T(1) / (kf * kf * (T)n2) : T(0);
+  m.k2 = kf * kf * (T)n2;
   m.amax = max(abs(nx), max(abs(ny), nz));
   return m;
 }
@@ -204,6 +208,7 @@ template <typename T> struct ColMode {
     m.k[2] = kz;
     const int n2 = nx * nx + nyz2;
     m.ik2 = n2 > 0 ? T(1) / (kf * kf * (T)n2) : T(0);
+    m.k2 = kf * kf * (T)n2;
     m.amax = max(abs(nx), ayz);
     return m;
   }
@@ -214,6 +219,7 @@ __device__ __forceinline__ C apply_mult(const MultDesc &d, C x, const ModeK<T> &
   T f = (T)d.scale;
   if (d.flags & M_AMP) f *= amp;
   if (d.flags & M_INVK2) f *= mk.ik2;
+  if (d.flags & M_GAUSS) f *= exp(-(T)d.gauss * mk.k2);
   if (d.flags & (M_INCUBE | M_OUTCUBE)) {
     const bool in = mk.amax < d.cube;
     if ((d.flags & M_INCUBE) ? !in : in) f = T(0);
