@@ -10,6 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libmujica_pm.so")
 
 PM_OK = 0
+PM_ERR_NONFINITE = 4
 STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_UNSUPPORTED", 3: "PM_ERR_CUDA",
           4: "PM_ERR_NONFINITE", 5: "PM_ERR_WORKSPACE", 6: "PM_ERR_LINESEARCH",
           7: "PM_ERR_DEVICE_STATUS"}

@@ -74,7 +74,12 @@ def reconstruct(plan, s0, data, R, iters, m=10, eps_max=1.0, c1=1e-4, max_halvin
                     info["resets_of_values"] += api.project_rank_match(plan, trial, L.PM_PROJECT, seed=seed,
                                                                        counter=counter)
                     counter += 1
-                ft, _ = api.pm_adjoint(plan, trial, data, R, grad_out=gt)
+                try:
+                    ft, _ = api.pm_adjoint(plan, trial, data, R, grad_out=gt)
+                except L.PMError as e:   # a trial with a non-finite loss is rejected like any other
+                    if e.status != L.PM_ERR_NONFINITE:
+                        raise
+                    ft = math.inf
                 info["evals"] += 1
                 if math.isfinite(ft) and ft <= f + c1 * eps * slope:
                     accepted = True

@@ -121,3 +121,22 @@ def test_ablation_harness(fake):
     # smaller caps make less progress on the quadratic after the same number of iterations
     fin = [runs[n]["curve"][-1][2] for n in ("L-BFGS", "L-BFGS-S-1", "L-BFGS-S-2", "L-BFGS-S-3")]
     assert fin[0] <= fin[1] <= fin[2] <= fin[3]
+
+
+def test_nonfinite_trial_is_rejected(fake, monkeypatch):
+    """A trial whose loss the library reports as non-finite is halved like a
+    failed Armijo test, not raised."""
+    from paper_2604_26823_gb300 import _lib as L
+    f, plan, s0, targets = fake
+    real = f.pm_adjoint
+    state = {"evals": 0}
+
+    def flaky(plan_, s, data, R, grad_out):
+        state["evals"] += 1
+        if state["evals"] == 2:                      # the first trial of the first iteration
+            raise L.PMError(L.PM_ERR_NONFINITE, "pm_adjoint", "loss is not finite")
+        return real(plan_, s, data, R, grad_out)
+
+    monkeypatch.setattr(f, "pm_adjoint", flaky)
+    _, loss, info = recon.reconstruct(plan, s0, None, None, 3, rom_every=0, project=False)
+    assert np.isfinite(loss) and info["halvings"] >= 1

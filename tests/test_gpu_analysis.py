@@ -34,7 +34,7 @@ def _dt(prec):
 
 
 def _dev(x, prec):
-    return torch.tensor(np.asarray(x), dtype=_dt(prec), device="cuda")
+    return torch.tensor(np.ascontiguousarray(x), dtype=_dt(prec), device="cuda")
 
 
 def _plan(api, n, prec, box):
