@@ -24,13 +24,11 @@ class FakeApi:
     """The library calls the driver makes, on CPU tensors."""
 
     def __init__(self):
-        self.calls = []          # (kind, mode or step length)
-        self.first_eval = []     # s of the first evaluation after each LBFGS creation
+        self.calls = []          # (kind, mode, step length or evaluated s)
 
     class LBFGS:
         def __init__(self, n, m=10, precision="f64"):
             self.o = OL.LBFGS(m)
-            self.fresh = True
 
         def close(self):
             pass
