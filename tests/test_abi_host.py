@@ -117,3 +117,30 @@ def test_host_power_table_matches_oracle(lib):
     rk, rp = C.linear_power_table()
     np.testing.assert_allclose(lnk, rk, rtol=0, atol=1e-13)
     np.testing.assert_allclose(lnp, rp, rtol=0, atol=1e-7)
+
+
+def test_analysis_and_annealing_argument_checks_without_gpu(lib):
+    """Argument errors of the plan-free entry points are reported before any
+    device call."""
+    z = ctypes.c_void_p(256)       # never dereferenced: the checks fail first
+    # coarsening: factor must be a power of two dividing n
+    assert lib.pm_coarsen(32, 3, 0, 0, z, z, None) == 1
+    assert lib.pm_coarsen(32, 64, 0, 0, z, z, None) == 1
+    assert lib.pm_coarsen(48, 2, 0, 0, z, z, None) == 1
+    assert lib.pm_coarsen(32, 2, 7, 0, z, z, None) == 1
+    assert lib.pm_coarsen(32, 2, 0, 2, z, z, None) == 1
+    assert lib.pm_coarsen(32, 2, 0, 0, None, z, None) == 1
+    # cosines / confusion: NULL arrays and bad precision
+    assert lib.pm_eigvec_cosines(10, 0, None, z, z, None) == 1
+    assert lib.pm_eigvec_cosines(10, 5, z, z, z, None) == 1
+    assert lib.pm_eigvec_cosines(-1, 0, z, z, z, None) == 1
+    assert lib.pm_confusion(10, 0, None, z, None, z, None) == 1
+    assert lib.pm_confusion(10, 0, z, z, None, None, None) == 1
+    # plan-bound entry points refuse a NULL plan
+    assert lib.pm_refine_noise(None, z, 16, z, z, None) == 1
+    assert lib.pm_tweb(None, z, 2.0, 0.16, z, None, None, None) == 1
+    assert lib.pm_smooth(None, z, 2.0, z, None) == 1
+    d = (ctypes.c_double * 4)()
+    assert lib.pm_power_spectra(None, z, None, 4, 0.1, 1.0, d, None, None, d, None) == 1
+    assert lib.pm_distance_table(0.3, 0.5, 1, d, d) == 1
+    assert lib.pm_distance_table(0.3, 1.5, 4, d, d) == 1
