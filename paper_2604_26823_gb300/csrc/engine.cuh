@@ -128,14 +128,15 @@ static __global__ void k_set_int(int *p, int v) { *p = v; }
 // ---- workspace layout -----------------------------------------------------
 // Leapfrog states holding the lightcone snapshots at a = 0.8 and 0.9 (the
 // one at a = 1 is the final state n_steps); false when the uniform grid
-// a_k = a_init + k (1 - a_init) / n_steps has no state there.
+// a_k = a_init + k (1 - a_init) / n_steps has no state there after the
+// initial one (a_init < 0.8 is required).
 constexpr int kLcTable = 2049;  // distance table points, a uniform on [0.5, 1]
 inline bool lightcone_states(const pm_config &c, int (&ks)[2]) {
   const double h = (1.0 - c.a_init) / c.n_steps;
   const double sa[2] = {0.8, 0.9};
   for (int j = 0; j < 2; ++j) {
     const double kf = std::nearbyint((sa[j] - c.a_init) / h);
-    if (!(kf >= 0.0 && kf < c.n_steps)) return false;
+    if (!(kf >= 1.0 && kf < c.n_steps)) return false;
     ks[j] = (int)kf;
     if (std::fabs(c.a_init + h * ks[j] - sa[j]) > 1e-9) return false;
   }

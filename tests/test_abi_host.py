@@ -109,6 +109,9 @@ def test_lightcone_validation_without_gpu(lib):
     # the lightcone is seen along the line of sight: rsd_axis must be 3
     assert lib.pm_workspace_bytes(ctypes.byref(api.Config(**dict(ok, rsd_axis=2)).to_c()), ctypes.byref(nb)) == 1
     assert lib.pm_workspace_bytes(ctypes.byref(api.Config(**dict(ok, n_steps=18)).to_c()), ctypes.byref(nb)) == 0
+    # the snapshots must be states after the initial condition
+    assert lib.pm_workspace_bytes(ctypes.byref(api.Config(**dict(ok, a_init=0.8, n_steps=2)).to_c()),
+                                  ctypes.byref(nb)) == 2
 
 
 def test_host_power_table_matches_oracle(lib):
