@@ -92,6 +92,15 @@ const char *pm_version(void);
 /* Number of CUDA kernel launches this library has issued since it was loaded
  * (all plans and threads; diagnostics, no counterpart in the paper). */
 int64_t pm_launch_count(void);
+/* Measured fused multiply-add rate of this GPU in the given precision
+ * (diagnostics: the arithmetic ceiling of the all-FP64 path, no counterpart in
+ * the paper).  One launch of 8 blocks per SM x 256 threads, each running 8
+ * independent FMA chains of `iters` steps (1 <= iters <= 1e6), timed with CUDA
+ * events on the stream; *tflops_out = 2 x FMAs / time in TFLOP/s.  scratch:
+ * device buffer of >= 8 bytes, written only in a case the arithmetic never
+ * reaches (it keeps the chains live).  Synchronises.  Errors:
+ * PM_ERR_INVALID_ARG, PM_ERR_CUDA. */
+pm_status pm_fma_rate(int32_t precision, int64_t iters, void *scratch, double *tflops_out, pm_stream_t stream);
 
 /* ---- host-side coefficients (no GPU) ----------------------------------- */
 

@@ -54,6 +54,7 @@ SIGNATURES = {
     "pm_last_error": (ctypes.c_char_p, []),
     "pm_version": (ctypes.c_char_p, []),
     "pm_launch_count": (ctypes.c_int64, []),
+    "pm_fma_rate": (_I32, [_I32, _I64, _P, _DP, _P]),
     "pm_linear_power_table": (_I32, [_D, _D, _D, _D, _D, _D, _D, _I32, _DP, _DP]),
     "pm_growth": (_I32, [_D, _I32, _DP, _DP, _DP, _DP, _DP]),
     "pm_distance_table": (_I32, [_D, _D, _I32, _DP, _DP]),

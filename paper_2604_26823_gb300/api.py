@@ -401,6 +401,16 @@ def lbfgs_step(state, x_new, g_new, d_out=None, stream=None):
     return d_out, gd.value, dn.value, bool(pushed.value)
 
 
+def pm_fma_rate(precision="f64", iters=4096, stream=None):
+    """Measured FMA rate of the GPU in TFLOP/s (diagnostics)."""
+    scratch = torch.empty(2, dtype=torch.float64, device="cuda")
+    r = ctypes.c_double()
+    L.check(L.load().pm_fma_rate(L.PM_PREC_F32 if precision == "f32" else L.PM_PREC_F64, int(iters),
+                                 ctypes.c_void_p(scratch.data_ptr()), ctypes.byref(r), _stream(stream)),
+            "pm_fma_rate")
+    return r.value
+
+
 def pm_axpy(alpha, x, y, out=None, stream=None):
     """out = y + alpha x (device kernel)."""
     if out is None:

@@ -82,6 +82,42 @@ const char *pm_last_error(void) { return g_err.c_str(); }
 const char *pm_version(void) { return "mujica-pm 0.1 (sm_103a)"; }
 int64_t pm_launch_count(void) { return pm::g_launches.load(); }
 
+pm_status pm_fma_rate(int32_t precision, int64_t iters, void *scratch, double *tflops_out, pm_stream_t stream) {
+  if (!scratch || !tflops_out || iters < 1 || iters > 1000000 ||
+      (precision != PM_PREC_F32 && precision != PM_PREC_F64)) {
+    pm::set_error("invalid FMA-rate arguments");
+    return PM_ERR_INVALID_ARG;
+  }
+  int dev = 0, sms = 0;
+  PM_CUDA_TRY(cudaGetDevice(&dev));
+  PM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int grid = 8 * sms, block = 256;
+  cudaEvent_t e0, e1;
+  PM_CUDA_TRY(cudaEventCreate(&e0));
+  PM_CUDA_TRY(cudaEventCreate(&e1));
+  float ms = 0.f;
+  cudaError_t err = cudaEventRecord(e0, s);
+  ::pm::note_launch();
+  if (precision == PM_PREC_F32)
+    pm::pw::k_fma_probe<float><<<grid, block, 0, s>>>(iters, (float *)scratch);
+  else
+    pm::pw::k_fma_probe<double><<<grid, block, 0, s>>>(iters, (double *)scratch);
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) {
+    pm::set_error(cudaGetErrorString(err));
+    return PM_ERR_CUDA;
+  }
+  const double fmas = (double)grid * block * 8.0 * (double)iters;
+  *tflops_out = 2.0 * fmas / (ms * 1e-3) / 1e12;
+  return PM_OK;
+}
+
 pm_status pm_linear_power_table(double omega_m, double omega_b, double h, double sigma8, double n_s,
                                 double k_min, double k_max, int32_t n_k, double *lnk, double *lnp) {
   if (!lnk || !lnp || n_k < 2 || !(k_min > 0) || !(k_max > k_min) || !(omega_m > 0) || !(omega_b >= 0) ||

@@ -256,6 +256,24 @@ __global__ void k_block_reduce(const T *__restrict__ in, int logc, int logr, boo
   out[j] = (T)acc;
 }
 
+// Eight independent FMA chains per thread, iters steps each (an arithmetic
+// rate probe); the result is stored only if it equals a value the chains
+// never produce, which keeps them from being optimised away.
+template <typename T> __global__ void k_fma_probe(int64_t iters, T *__restrict__ sink) {
+  T a[8];
+  const T m = T(0.999999), c = T(1e-7);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = T(threadIdx.x + j) * T(1e-3);
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  if (s == T(-1.25e30)) sink[0] = s;
+}
+
 // out = y + a * x
 template <typename T>
 __global__ void k_axpy(const T *__restrict__ x, const T *__restrict__ y, double a, T *__restrict__ out, int64_t n) {

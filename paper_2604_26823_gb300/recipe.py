@@ -8,7 +8,9 @@ Appendix A), beyond the benchmark workload:
               Poisson likelihood;
   coarse      the same at (n/2)^3, the annealing stage's mesh;
   analysis    P(k) auto + cross spectra (32 bins) and the T-web
-              (R_sm = 2 Mpc/h, lambda_th = 0.16) of two n^3 fields.
+              (R_sm = 2 Mpc/h, lambda_th = 0.16) of two n^3 fields;
+  fma_tflops  the measured FP32 / FP64 FMA rates (the arithmetic ceiling
+              against which the all-FP64 path is read).
 
 Every number is CUDA-event time on the launching (default) stream after
 warm-up; inputs are resident on the device.  One JSON line:
@@ -89,6 +91,7 @@ def main():
     torch.cuda.empty_cache()
     ms_pk, ms_tw = analysis_times(args.n, args.box, args.evals, lnk, lnp)
     res["analysis"] = {"power_spectra_ms": ms_pk, "tweb_ms": ms_tw}
+    res["fma_tflops"] = {"f32": api.pm_fma_rate("f32", 16384), "f64": api.pm_fma_rate("f64", 4096)}
     res["peak_allocated_gb"] = torch.cuda.max_memory_allocated() / 1e9
     print(json.dumps(res), flush=True)
 

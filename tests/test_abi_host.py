@@ -145,5 +145,8 @@ def test_analysis_and_annealing_argument_checks_without_gpu(lib):
     assert lib.pm_smooth(None, z, 2.0, z, None) == 1
     d = (ctypes.c_double * 4)()
     assert lib.pm_power_spectra(None, z, None, 4, 0.1, 1.0, d, None, None, d, None) == 1
+    assert lib.pm_fma_rate(2, 100, z, d, None) == 1
+    assert lib.pm_fma_rate(1, 0, z, d, None) == 1
+    assert lib.pm_fma_rate(1, 100, None, d, None) == 1
     assert lib.pm_distance_table(0.3, 0.5, 1, d, d) == 1
     assert lib.pm_distance_table(0.3, 1.5, 4, d, d) == 1
