@@ -20,7 +20,6 @@ warm-up; inputs are resident on the device.  One JSON line:
 import argparse
 import json
 
-import numpy as np
 import torch
 
 from . import api, build, inputs, recon
