@@ -15,11 +15,27 @@ real-space rank-order matching on every 20th step, the paper's schedule),
 and pm_adjoint (forward model + gradient) at the trial point.  Each step is
 exactly one gradient evaluation, so steps/s = gradient evals/s.
 
+The timed region runs with the library's kernel timing off.  Per-kernel-class
+times (CUDA events around every launch) come from a separate pass of the same
+steps after it; the roofline line takes the dominant class's algorithmic
+bytes per launch (the method's arrays read and written once, FP32 words)
+over its mean launch time, against the measured HBM copy bandwidth.
+
+Extra keys: the all-FP64 GPU path (with the measured FP32 / FP64 FMA rates
+and the FFT passes' FP64 arithmetic rate), the checkpointed 512^3
+configuration, the paper's run recipe (18 steps of da = 0.05 with the
+lightcone and the radial redshift-space shift at 256^3; the 128^3 annealing
+stage), cuFFT as a comparison of one FFT pair, the end-to-end rate through
+the C ABI with host buffers, and the FP64 oracle on the host cores.
+
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
 """
 import argparse
+import hashlib
 import json
+import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -36,12 +52,9 @@ UNIT = "gradient evals/s"
 N, BOX, STEPS_PM = 256, 500.0, 10
 NBAR = 1e-3
 ROM_EVERY = 20
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the cotangent-paint launches of one gradient evaluation of this
-# workload, k = 9 .. 0) from one ncu capture of the kernel as it stands;
-# profiles/deposit_traffic_masked_recon_256.md gives the command.  Set to None
-# when the kernel changes.
-NCU_TRAFFIC = {"adj_paint": 1152.3e6}
+OBSERVER = (250.0, 250.0, -150.0)    # Mpc/h, box coordinates: outside the box, looking along +z
+PROF_STEPS = 5                       # steps of the separate kernel-timing pass
+
 
 def config(api, nbar_cell, precision="f32"):
     from paper_2604_26823_gb300 import recon
@@ -134,9 +147,25 @@ def barrier(ws):
         dist.barrier()
 
 
-def oracle_sample(n_small=64):
-    """One FP64 oracle gradient of the same physics at n_small^3 (same cell
-    size), seconds; scaled to 256^3 by the cell count."""
+# ---- the FP64 oracle on the host cores -----------------------------------------
+
+def host_cpu():
+    """(logical cores, CPU model name) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return os.cpu_count(), model
+
+
+def oracle_gradient_seconds(n_small):
+    """Seconds of one FP64 oracle gradient of the benchmark's physics at
+    n_small^3 (same cell size, 10 steps, masked Poisson), single-threaded."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import cosmology as OC
     from oracle import model as OM
@@ -152,23 +181,47 @@ def oracle_sample(n_small=64):
     OC.growth([0.1], 0.25)  # warm the growth cache outside the timing
     t0 = time.perf_counter()
     OM.gradient(s, cfg, lnk, lnp, counts, resp)
-    return time.perf_counter() - t0, (N / n_small) ** 3
+    return time.perf_counter() - t0
+
+
+def oracle_scaling():
+    """One oracle gradient at 64^3 and one at 128^3: (t64, t128, r = t128 / t64).
+    The time per doubling of n at the larger sizes is r (t ~ n^(log2 r)), so a
+    256^3 gradient takes t128 * r."""
+    t64 = oracle_gradient_seconds(64)
+    t128 = oracle_gradient_seconds(128)
+    return t64, t128, t128 / t64
+
+
+def cpu_baseline():
+    t64, t128, r = oracle_scaling()
+    t256 = t128 * r
+    cores, model = host_cpu()
+    return {"value": 1.0 / t256, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one FP64 oracle gradient (2LPT + 10 steps, masked Poisson, same cell size) at 64^3 took "
+                       f"{t64:.2f} s and at 128^3 {t128:.2f} s; time per doubling of n r = t128/t64 = {r:.2f} "
+                       f"(t ~ n^{math.log2(r):.2f}), so 256^3 = t128 x r = {t256:.0f} s; 1 thread of a {cores}-core "
+                       f"{model or 'unknown'} host"),
+            "t64_s": t64, "t128_s": t128, "host_cores": cores, "host_cpu": model}
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle as it stands on one host core.  Each
+    step is one 64^3 oracle gradient, scaled to 256^3 by r^2 with r = t128 /
+    t64 measured once (before the warm-up steps) from a 128^3 gradient."""
     if rank != 0:
         return
-    n_small = 32
+    t64, t128, r = oracle_scaling()
+    scale = r * r
     for _ in range(args.warmup):
-        oracle_sample(n_small)
-    times = []
-    for _ in range(args.steps):
-        t, scale = oracle_sample(n_small)
-        times.append(t * scale)
+        oracle_gradient_seconds(64)
+    times = [oracle_gradient_seconds(64) * scale for _ in range(args.steps)]
     per = float(np.mean(times))
     value = 1.0 / per
-    sample = (f"one FP64 oracle gradient (2LPT + 10 steps, Poisson, same cell size) at {n_small}^3 per step, "
-              f"time scaled x{int((N / n_small) ** 3)} by cell count to 256^3")
+    cores, model = host_cpu()
+    sample = (f"one FP64 oracle gradient (2LPT + 10 steps, masked Poisson, same cell size) at 64^3 per step, "
+              f"scaled to 256^3 by (t128/t64)^2 = {scale:.1f} (t64 {t64:.2f} s, t128 {t128:.2f} s measured "
+              f"before the warm-up); 1 thread of a {cores}-core {model or 'unknown'} host")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -179,26 +232,68 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---- DRAM traffic of a kernel class from its committed ncu summary --------------
+
+def profile_traffic(kernel):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    a kernel class from profiles/<kernel>_traffic_masked_recon_256.md, scaled
+    as that summary states; None when there is no summary or when the kernel's
+    source files changed since the capture (the summary records their
+    SHA-256)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic_masked_recon_256.md")
+    if not os.path.exists(path):
+        return None, "no committed capture"
+    text = open(path).read()
+    m = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", text, re.M)
+    srcs = re.search(r"^sources:\s*(.+)$", text, re.M)
+    sha = re.search(r"^sources_sha256:\s*([0-9a-f]+)", text, re.M)
+    if not (m and srcs and sha):
+        return None, "summary without traffic / source hash"
+    h = hashlib.sha256()
+    for f in srcs.group(1).split():
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != sha.group(1):
+        return None, "kernel changed since the capture"
+    return float(m.group(1)), os.path.relpath(path, ROOT)
+
+
+def sources_sha256(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+# ---- timed pieces -------------------------------------------------------------------
+
+def event_ms(fn, reps, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
 def fft_comparison(api, plan, s, reps=20):
+    """cuFFT as a comparison only: the linear field delta_L = IFFT[A(k) FFT[s]]
+    through the library's pencil passes (one r2c, y, fused x with the
+    amplitude multiplier, y, c2r) against torch.fft (cuFFT) rfftn * A irfftn
+    on the same 256^3 FP32 mesh (the cuFFT side skips the DC / Nyquist
+    conventions, so only the times are compared)."""
     import torch
     out = torch.empty_like(s)
     amp = torch.rand((N, N, N // 2 + 1), dtype=torch.float32, device="cuda")
-    ev = lambda: torch.cuda.Event(enable_timing=True)
-
-    def timed(f):
-        for _ in range(3):
-            f()
-        a, b = ev(), ev()
-        torch.cuda.synchronize()
-        a.record()
-        for _ in range(reps):
-            f()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
-    ours = timed(lambda: api.pm_linear_field(plan, s, out=out))
-    cufft = timed(lambda: torch.fft.irfftn(torch.fft.rfftn(s) * amp, s=(N, N, N)))
+    ours = event_ms(lambda: api.pm_linear_field(plan, s, out=out), reps, 3)
+    cufft = event_ms(lambda: torch.fft.irfftn(torch.fft.rfftn(s) * amp, s=(N, N, N)), reps, 3)
     return {"op": "linear field: real 256^3 -> spectrum x A(k) -> real (FP32)", "library_ms": ours,
             "cufft_ms": cufft, "note": "comparison only; cuFFT is not used on the path"}
 
@@ -220,16 +315,7 @@ def run_ckpt512(api, inputs, lnk, lnp, evals=3):
     d = torch.from_numpy(inputs.normal_field(n, 3)).cuda()
     R = torch.ones((n, n, n), dtype=torch.float32, device="cuda")
     g = torch.empty_like(s)
-    api.pm_adjoint(plan, s, d, R, grad_out=g)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(evals):
-        api.pm_adjoint(plan, s, d, R, grad_out=g)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / evals
+    ms = event_ms(lambda: api.pm_adjoint(plan, s, d, R, grad_out=g), evals, 1)
     free1, _ = torch.cuda.mem_get_info()
     out = {"workload": "ckpt-512", "n_mesh": n, "box": 1000.0, "pm_steps": STEPS_PM, "checkpoint_every": 2,
            "value": 1e3 / ms, "unit": UNIT, "ms_per_eval": ms, "evals": evals,
@@ -239,6 +325,68 @@ def run_ckpt512(api, inputs, lnk, lnp, evals=3):
     plan.close()
     del plan, s, d, R, g
     torch.cuda.empty_cache()
+    return out
+
+
+def run_recipe(api, inputs, recon, lnk, lnp, evals=5, coarse_iters=25):
+    """The paper's run recipe (Sec. 2.2.1 items 2-3, Sec. 3, Appendix A) on the
+    benchmark's mock geometry:
+      lightcone_256: pm_adjoint at 256^3 with 18 leapfrog steps (da = 0.05 from
+        a = 0.1), snapshots at a = 0.8, 0.9, 1, every particle observed on the
+        past light cone and shifted along the line of sight from the observer,
+        masked Poisson likelihood;
+      anneal_128: the low-resolution stage of the annealed reconstruction --
+        128^3 cells of 3.9 Mpc/h (counts summed and R averaged over 2^3 blocks,
+        nbar per cell x 8), augmented L-BFGS with rank-order matching every 5
+        iterations -- in iterations and gradient evaluations per second."""
+    import torch
+    dev = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+    R_h, _, counts_h, nbar = recon.masked_mock(N, BOX, n_steps=18, nbar=NBAR, lnk=lnk, lnp=lnp)
+    cfg = recon.mock_config(N, BOX, nbar, n_steps=18)
+    cfg.rsd_axis, cfg.lightcone, cfg.observer = 3, True, OBSERVER
+    plan = api.Plan(cfg, lnk, lnp)
+    s, c, r = dev(inputs.white_noise(N, 2)), dev(counts_h), dev(R_h)
+    g = torch.empty_like(s)
+    ms = event_ms(lambda: api.pm_adjoint(plan, s, c, r, grad_out=g), evals)
+    out = {"lightcone_256": {"value": 1e3 / ms, "unit": UNIT, "ms_per_eval": ms, "pm_steps": 18,
+                             "observer": OBSERVER, "workspace_gb": plan.workspace_bytes / 1e9}}
+    plan.close()
+    del plan, s, g
+    torch.cuda.empty_cache()
+    # the annealing stage at 128^3
+    f = 2
+    nc = N // f
+    c_c, R_c = api.pm_coarsen(c, f), api.pm_coarsen(r, f, mean=True)
+    cfg_c = recon.mock_config(nc, BOX, nbar * f ** 3, n_steps=18)
+    plan_c = api.Plan(cfg_c, lnk, lnp)
+    nreal = api.pm_count_positive(plan_c, R_c)
+    fcounts = api.pm_rom_fourier_counts(plan_c)
+    tr = {it: (dev(inputs.sorted_normal_targets(nreal, 7 + it)),
+               dev(inputs.sorted_normal_targets_per_bin(fcounts, 7 + it))) for it in range(5, coarse_iters + 1, 5)}
+    s0 = dev(inputs.white_noise(nc, 2))
+    recon.reconstruct(plan_c, s0, c_c, R_c, 2, rom_every=0)      # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, loss, info = recon.reconstruct(plan_c, s0, c_c, R_c, coarse_iters, rom_every=5, rom_targets=lambda it: tr[it])
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    out["anneal_128"] = {"iterations_per_s": coarse_iters / sec, "evals_per_s": info["evals"] / sec,
+                         "iterations": coarse_iters, "gradient_evals": info["evals"], "rom_every": 5,
+                         "pm_steps": 18, "cell_mpc_h": BOX / nc, "final_loss": loss}
+    plan_c.close()
+    del plan_c
+    torch.cuda.empty_cache()
+    return out
+
+
+def kernel_classes(api, prof, steps):
+    """Per kernel class, per step: time, launches, algorithmic and implementation
+    bytes, and the algorithmic GB/s."""
+    out = {}
+    for k, (ms, n, b, ib, fl) in prof.items():
+        out[k] = {"ms_per_step": ms / steps, "launches": n, "alg_bytes_per_launch": b / n if n else None,
+                  "impl_bytes_per_launch": ib / n if n else None,
+                  "alg_GBps": (b / (ms / 1e3) / 1e9) if ms else None, "flops": fl}
     return out
 
 
@@ -289,7 +437,6 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     barrier(ws)
     clocks = Clocks(local)
-    api.pm_profile(plan, True, 200000)
     launches0 = lib.pm_launch_count()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -305,43 +452,55 @@ def run_ours(args, ws, rank, local):
     launches = lib.pm_launch_count() - launches0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    prof = {c: api.pm_profile_read(plan, c) for c in api.PROFILE_CLASSES}
-    api.pm_profile(plan, False)
     barrier(ws)
     value = whole_job_rate(args.steps, ws, ms / 1e3)
     ms_max = ws * args.steps / value * 1e3
 
-    # dominant kernel class: algorithmic bytes (recorded per launch by the
-    # library) over its event-timed duration, against the measured HBM peak
+    # kernel-class times from a separate pass of the same schedule (steps 0 ..
+    # PROF_STEPS - 1, so the rank-order matching of step 0 is included), CUDA
+    # events around every launch of a profiled class
+    state["it"] = 0
+    api.pm_profile(plan, True, 200000)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(PROF_STEPS):
+        step(plan, st, state, counts, R, t_real, t_four)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = pe0.elapsed_time(pe1)
+    prof = {c: api.pm_profile_read(plan, c) for c in api.PROFILE_CLASSES}
+    api.pm_profile(plan, False)
+    classes = kernel_classes(api, prof, PROF_STEPS)
+
+    # roofline of the dominant class: algorithmic bytes per launch over the
+    # mean launch time, against the measured HBM copy bandwidth
     peak, peak_src = 6800.0, "fallback (6.8 TB/s)"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peak, peak_src = float(json.load(fh)["hbm_gbs"]), "measured"
+            peak, peak_src = float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
         pass
-    classes = {k: {"ms_total": v[0], "launches": v[1], "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] else None}
-               for k, v in prof.items()}
-    # byte model of the step: the algorithmic bytes the library records for its
-    # profiled kernel classes (inputs read once, outputs written once), per
-    # step, over the measured step time (end-to-end effective bandwidth)
-    alg_step = sum(v[2] for v in prof.values()) / args.steps
-    bytes_model = {"algorithmic_bytes_per_step": alg_step, "profiled_classes_ms_per_step":
-                   sum(v[0] for v in prof.values()) / args.steps,
-                   "effective_GBps": alg_step / (ms / args.steps / 1e3) / 1e9}
     dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_n, dom_b = prof[dom]
-    roof = None
-    if dom_n:
-        achieved = dom_b / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "peak_source": peak_src, "launches": dom_n,
-                "mean_launch_ms": dom_ms / dom_n, "algorithmic_bytes_per_launch": dom_b / dom_n,
-                "share_of_step": dom_ms / ms}
-    # FP64 path: same workload and schedule
+    dom_ms, dom_n, dom_b, dom_ib, _ = prof[dom]
+    traffic, traffic_src = profile_traffic(dom)
+    achieved = dom_b / dom_n / (dom_ms / dom_n / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": peak_src,
+            "launches": dom_n, "mean_launch_ms": dom_ms / dom_n, "algorithmic_bytes_per_launch": dom_b / dom_n,
+            "impl_bytes_per_launch": dom_ib / dom_n, "share_of_step": dom_ms / prof_ms,
+            "timing": f"CUDA events around each launch in a separate pass of {PROF_STEPS} steps after the timed region"}
+    alg_step = sum(v[2] for v in prof.values()) / PROF_STEPS
+    bytes_model = {"algorithmic_bytes_per_step": alg_step,
+                   "profiled_classes_ms_per_step": sum(v[0] for v in prof.values()) / PROF_STEPS,
+                   "effective_GBps": alg_step / (ms / args.steps / 1e3) / 1e9,
+                   "effective_frac": alg_step / (ms / args.steps / 1e3) / 1e9 / peak}
+
+    # FP64 path: same workload and schedule; its FFT passes against the measured FP64 FMA rate
     fp64 = None
     if not args.no_fp64:
         del plan
         torch.cuda.empty_cache()
+        fma = {"f32_tflops": api.pm_fma_rate("f32", 16384), "f64_tflops": api.pm_fma_rate("f64", 4096)}
         plan64 = api.Plan(config(api, nbar_cell, "f64"), lnk, lnp)
         d64 = lambda x: torch.as_tensor(x).to(device="cuda", dtype=torch.float64)
         st64 = api.LBFGS(N ** 3, m=10, precision="f64")
@@ -352,24 +511,28 @@ def run_ours(args, ws, rank, local):
         _, S64["g"] = api.pm_adjoint(plan64, S64["s"], c64, R64, grad_out=S64["g"])
         step(plan64, st64, S64, c64, R64, tr64, tf64)
         S64["it"] = 0
-        torch.cuda.synchronize()
         k64 = max(2, min(args.steps, 4))
-        t0 = time.perf_counter()
-        for _ in range(k64):
-            step(plan64, st64, S64, c64, R64, tr64, tf64)
-        torch.cuda.synchronize()
-        fp64 = {"value": k64 / (time.perf_counter() - t0), "unit": UNIT, "steps": k64}
+        ms64 = event_ms(lambda: step(plan64, st64, S64, c64, R64, tr64, tf64), k64, 0)
+        S64["it"] = 1
+        api.pm_profile(plan64, True, 20000)
+        step(plan64, st64, S64, c64, R64, tr64, tf64)
+        p64 = {c: api.pm_profile_read(plan64, c) for c in api.PROFILE_CLASSES}
+        api.pm_profile(plan64, False)
+        fft_cls = ("z_r2c", "col", "x_fused", "z_c2r")
+        fft_ms = sum(p64[c][0] for c in fft_cls)
+        fft_fl = sum(p64[c][4] for c in fft_cls)
+        fp64 = {"value": 1e3 / ms64, "unit": UNIT, "steps": k64, "fma": fma,
+                "kernel_classes": kernel_classes(api, p64, 1),
+                "fft_roofline": {"bound": "alu", "achieved": fft_fl / (fft_ms / 1e3) / 1e12,
+                                 "peak": fma["f64_tflops"], "unit": "TFLOP/s",
+                                 "frac": fft_fl / (fft_ms / 1e3) / 1e12 / fma["f64_tflops"],
+                                 "flops_per_step": fft_fl, "ms_per_step": fft_ms,
+                                 "note": "FFT passes of one step (5 L log2 L per complex FFT of length L, half for "
+                                         "real); peak = pm_fma_rate FP64 on this GPU"}}
         del plan64, st64, S64
         torch.cuda.empty_cache()
         plan = api.Plan(cfg, lnk, lnp)
 
-    # checkpointed 512^3 configuration (1000 Mpc/h, 10 steps, states kept every
-    # 2 steps): gradient evals/s and peak device memory
-    # cuFFT as a comparison only: the linear field delta_L = IFFT[A(k) FFT[s]]
-    # through the library's pencil passes (one r2c, y, fused x with the
-    # amplitude multiplier, y, c2r) against torch.fft (cuFFT) rfftn * A irfftn
-    # on the same 256^3 FP32 mesh (the cuFFT side skips the DC / Nyquist
-    # conventions, so only the times are compared)
     fft_cmp = fft_comparison(api, plan, state["s"])
 
     ck512 = None
@@ -377,6 +540,13 @@ def run_ours(args, ws, rank, local):
         del plan
         torch.cuda.empty_cache()
         ck512 = run_ckpt512(api, inputs, lnk, lnp)
+        plan = api.Plan(cfg, lnk, lnp)
+
+    recipe = None
+    if not args.no_recipe:
+        del plan
+        torch.cuda.empty_cache()
+        recipe = run_recipe(api, inputs, recon, lnk, lnp)
         plan = api.Plan(cfg, lnk, lnp)
 
     # end to end through the public API with pinned host buffers: every step
@@ -408,10 +578,7 @@ def run_ours(args, ws, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        t, scale = oracle_sample(64)
-        cpu = {"value": 1.0 / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 oracle gradient (same physics and cell size) at 64^3 took {t:.1f} s, "
-                         f"scaled x{int(scale)} by cell count to 256^3"}
+        cpu = cpu_baseline()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -420,11 +587,35 @@ def run_ours(args, ws, rank, local):
                 "config": {"workload": "masked-recon-256", "n_mesh": N, "n_particles": N ** 3, "box": BOX,
                            "pm_steps": STEPS_PM, "lbfgs_m": 10, "rom_every": ROM_EVERY,
                            "likelihood": "poisson", "galaxies": n_gal, "selection_volume_frac": vol_frac,
-                           "parallelism": f"replicas x{ws}", "l2": "working set ~7 GB >> 129 MB L2 (no flush)"},
-                "fp64_path": fp64, "checkpointed_512": ck512, "fft_vs_cufft": fft_cmp, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-                "gpu_launches": int(launches), "clocks": clk, "kernel_classes": classes, "bytes_model": bytes_model,
-                "final_loss": losses[-1]}
+                           "parallelism": f"replicas x{ws}", "l2": "working set ~8 GB >> 129 MB L2 (no flush)",
+                           "kernel_timing": "off in the timed region"},
+                "fp64_path": fp64, "checkpointed_512": ck512, "recipe": recipe, "fft_vs_cufft": fft_cmp, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clk,
+                "kernel_classes": classes, "bytes_model": bytes_model, "final_loss": losses[-1]}
         print(json.dumps(line), flush=True)
+
+
+def run_profile_workload(args):
+    """A fixed, untimed workload for profilers (ncu): ``--profile-evals``
+    gradient evaluations (pm_adjoint) of the masked Poisson problem at
+    --profile-n^3 (box scaled with n so the cell stays 500/256 Mpc/h),
+    --pm-steps leapfrog steps, FP32 path, after the mock and the plan are
+    built."""
+    import torch
+    from paper_2604_26823_gb300 import api, build, inputs, recon
+    build.build()
+    n, box = args.profile_n, BOX * args.profile_n / N
+    lnk, lnp = api.pm_linear_power_table()
+    R, _, counts, nbar = recon.masked_mock(n, box, n_steps=args.pm_steps, lnk=lnk, lnp=lnp)
+    plan = api.Plan(recon.mock_config(n, box, nbar, n_steps=args.pm_steps), lnk, lnp)
+    dev = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+    s0, c, r = dev(inputs.white_noise(n, 2)), dev(counts), dev(R)
+    loss = None
+    for _ in range(args.profile_evals):
+        loss, _ = api.pm_adjoint(plan, s0, c, r)
+    torch.cuda.synchronize()
+    print(f"profile workload n={n} pm_steps={args.pm_steps} evals={args.profile_evals} loss={loss:.6f} "
+          f"peak_allocated_gb={torch.cuda.max_memory_allocated() / 1e9:.2f}", flush=True)
 
 
 def main():
@@ -436,7 +627,15 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-512", action="store_true", help="skip the checkpointed 512^3 measurement")
+    ap.add_argument("--no-recipe", action="store_true", help="skip the lightcone / annealing recipe timings")
+    ap.add_argument("--profile-evals", type=int, default=0,
+                    help="run only this many untimed gradient evaluations (a workload for ncu) and exit")
+    ap.add_argument("--profile-n", type=int, default=N, help="mesh of the --profile-evals workload")
+    ap.add_argument("--pm-steps", type=int, default=STEPS_PM, help="leapfrog steps of the --profile-evals workload")
     args = ap.parse_args()
+    if args.profile_evals:
+        run_profile_workload(args)
+        return
     ws, rank, local = (1, 0, 0) if args.impl == "reference" and int(os.environ.get("WORLD_SIZE", "1")) == 1 \
         else dist_setup()
     if args.impl == "reference":

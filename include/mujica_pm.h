@@ -208,12 +208,15 @@ pm_status pm_refine_noise(pm_plan *plan, const void *s_coarse, int32_t n_coarse,
  * of integer wave vector m, |k| = (2 pi / box) |m|, falls in bin
  * floor((|k| - k_min) / dk), dk = (k_max - k_min) / n_bins, when that lies in
  * [0, n_bins).  Host outputs of n_bins doubles: p_aa, counts (required), p_bb,
- * p_ab (nullable; 0 when b is NULL); empty bins give NaN.  r_c = p_ab /
- * sqrt(p_aa p_bb).  Uses the plan's workspace; synchronises the stream.  Bin
- * sums are FP64 atomics, so the last bits may differ between calls.  Errors:
- * PM_ERR_INVALID_ARG (n_bins outside [1, 1024], k_max <= k_min), PM_ERR_CUDA. */
+ * p_ab (nullable; 0 when b is NULL), r_c (nullable): the cross-correlation
+ * coefficient r_c = p_ab / sqrt(p_aa p_bb) of Sec. 3.2 (NaN when b is NULL);
+ * empty bins give NaN.  Uses the plan's workspace; synchronises the stream.
+ * Bin sums are FP64 atomics, so the last bits may differ between calls.
+ * Errors: PM_ERR_INVALID_ARG (n_bins outside [1, 1024], k_max <= k_min),
+ * PM_ERR_CUDA. */
 pm_status pm_power_spectra(pm_plan *plan, const void *a, const void *b, int32_t n_bins, double k_min, double k_max,
-                           double *p_aa, double *p_bb, double *p_ab, double *counts, pm_stream_t stream);
+                           double *p_aa, double *p_bb, double *p_ab, double *counts, double *r_c,
+                           pm_stream_t stream);
 
 /* Gaussian smoothing out = IFFT[exp(-|k|^2 r_sm^2 / 2) FFT(in)] (r_sm in Mpc/h,
  * >= 0), device arrays [n^3] of the plan's precision (in-place allowed). */
@@ -256,14 +259,19 @@ pm_status pm_coarsen(int32_t n, int32_t factor, int32_t precision, int32_t mean,
  * on brackets every launch of the profiled kernel classes on its stream
  * (up to capacity launches); pm_profile(plan, 0, 0) stops recording.
  * pm_profile_read sums, over the recorded launches of one class, the elapsed
- * time, the launch count and the algorithmic bytes each launch must move
- * (its inputs read once and outputs written once) (synchronises).
+ * time, the launch count, the algorithmic bytes each launch must move (the
+ * method's inputs read once and outputs written once, meshes and particle
+ * arrays as FP32 / FP64 words) and (impl_bytes_total, nullable) the bytes of
+ * the implementation's own arrays (64-bit fixed-point meshes, the padded
+ * force mesh, binning words) and (flops_total, nullable) the floating-point
+ * operations of the FFT passes (5 L log2 L per complex FFT of length L, half
+ * for a real one; 0 for the other classes) (synchronises).
  * Classes: 0 fused readout+kick+drift+paint, 1 z-pass r2c, 2 column pass,
- * 3 x-pass with multipliers, 4 z-pass c2r, 5 adjoint 3-channel paint,
- * 6 adjoint gather, 7 likelihood. */
+ * 3 x-pass with multipliers, 4 z-pass c2r, 5 adjoint 3-channel paint
+ * (with its tile binning), 6 adjoint gather, 7 likelihood. */
 pm_status pm_profile(pm_plan *plan, int32_t enable, int32_t capacity);
 pm_status pm_profile_read(pm_plan *plan, int32_t kernel_class, double *ms_total, int64_t *launches,
-                          double *bytes_total);
+                          double *bytes_total, double *impl_bytes_total, double *flops_total);
 
 /* ---- projection and rank-order matching (Sec. 2.3.1, Sec. 2.3.2) ------- */
 
@@ -320,7 +328,11 @@ pm_status lbfgs_reset(lbfgs_state *st);
  * with H0 = gamma I (gamma = s.y / y.y of the newest pair, 1 without pairs);
  * if g.d >= 0 the pairs are dropped and d = -g.  Host outputs (nullable):
  * gdotd_out = g.d, dnorm_out = |d|, pushed_out = whether a pair was stored.
- * Dot products accumulate in FP64.  Synchronises. */
+ * Dot products: FP64 vectors accumulate in FP64; FP32 vectors form each
+ * product exactly (p + e by FMA) and sum it per thread in a compensated FP32
+ * pair (Knuth's TwoSum), converted to FP64 once per thread, then every thread's
+ * partial is added in FP64 in a fixed order (deterministic; within ~1e-13 of
+ * sum |x y|, far below the 6e-8 rounding of the FP32 vectors).  Synchronises. */
 pm_status lbfgs_step(lbfgs_state *st, const void *x_new, const void *g_new, void *d_out,
                      double *gdotd_out, double *dnorm_out, int32_t *pushed_out,
                      pm_stream_t stream);

@@ -21,7 +21,11 @@ Realistic Redshift Surveys with Augmented Optimization"):
   and rank-order matching R (Sec. 2.3.2) in real and Fourier space.
 * ``lbfgs`` -- the L-BFGS two-loop recursion and the projected
   backtracking line search (Sec. 2.3.1, Appendix B Table 1).
-* ``power`` -- shell-averaged power / cross spectra (Sec. 3.2, Eq. r_c).
+* ``anneal`` -- the resolution transfer of the white noise and the coarse
+  data of the annealed reconstruction (Sec. 3, opening).
+* ``analysis`` -- binned power / cross spectra and r_c (Sec. 3.2), Gaussian
+  smoothing, the T-web classification, eigenvector cosines and the confusion
+  matrix (Sec. 3.3).
 
 Parity unpinned: the shape of the Eisenstein-Hu no-wiggle transfer function
 between its k->0 limit and its normalisation is not pinned by any printed

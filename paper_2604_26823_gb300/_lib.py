@@ -71,13 +71,13 @@ SIGNATURES = {
     "pm_expected_counts": (_I32, [_P, _P, _P, _P, _P]),
     "pm_refine_noise": (_I32, [_P, _P, _I32, _P, _P, _P]),
     "pm_coarsen": (_I32, [_I32, _I32, _I32, _I32, _P, _P, _P]),
-    "pm_power_spectra": (_I32, [_P, _P, _P, _I32, _D, _D, _DP, _DP, _DP, _DP, _P]),
+    "pm_power_spectra": (_I32, [_P, _P, _P, _I32, _D, _D, _DP, _DP, _DP, _DP, _DP, _P]),
     "pm_smooth": (_I32, [_P, _P, _D, _P, _P]),
     "pm_tweb": (_I32, [_P, _P, _D, _D, _P, _P, _P, _P]),
     "pm_eigvec_cosines": (_I32, [ctypes.c_int64, _I32, _P, _P, _P, _P]),
     "pm_confusion": (_I32, [ctypes.c_int64, _I32, _P, _P, _P, _P, _P]),
     "pm_profile": (_I32, [_P, _I32, _I32]),
-    "pm_profile_read": (_I32, [_P, _I32, _DP, _I64P, _DP]),
+    "pm_profile_read": (_I32, [_P, _I32, _DP, _I64P, _DP, _DP, _DP]),
     "pm_rom_fourier_counts": (_I32, [_P, _I64P]),
     "pm_count_positive": (_I32, [_P, _P, _I64P, _P]),
     "project_rank_match": (_I32, [_P, _P, _U32, _P, _P, _P, _U64, _U64, _I64P, _P]),

@@ -355,7 +355,8 @@ pm_status pm_coarsen(int32_t n, int32_t factor, int32_t precision, int32_t mean,
 }
 
 pm_status pm_power_spectra(pm_plan *plan, const void *a, const void *b, int32_t n_bins, double k_min, double k_max,
-                           double *p_aa, double *p_bb, double *p_ab, double *counts, pm_stream_t stream) {
+                           double *p_aa, double *p_bb, double *p_ab, double *counts, double *r_c,
+                           pm_stream_t stream) {
   if (!plan || !a || !p_aa || !counts || n_bins < 1 || n_bins > 1024 || !std::isfinite(k_min) ||
       !std::isfinite(k_max) || !(k_max > k_min)) {
     pm::set_error("invalid power spectrum arguments (n_bins in [1, 1024], k_max > k_min, outputs)");
@@ -378,6 +379,8 @@ pm_status pm_power_spectra(pm_plan *plan, const void *a, const void *b, int32_t 
     if (p_bb) p_bb[j] = h[n_bins + j];
     if (p_ab) p_ab[j] = h[2 * n_bins + j];
     counts[j] = h[3 * n_bins + j];
+    // cross-correlation coefficient r_c = P_ab / sqrt(P_aa P_bb) (Sec. 3.2)
+    if (r_c) r_c[j] = b ? h[2 * n_bins + j] / std::sqrt(h[j] * h[n_bins + j]) : NAN;
   }
   return PM_OK;
 }
@@ -458,13 +461,13 @@ pm_status pm_profile(pm_plan *plan, int32_t enable, int32_t capacity) {
 }
 
 pm_status pm_profile_read(pm_plan *plan, int32_t kernel_class, double *ms_total, int64_t *launches,
-                          double *bytes_total) {
+                          double *bytes_total, double *impl_bytes_total, double *flops_total) {
   if (!plan || kernel_class < 0 || kernel_class >= pm::P_NCLASS || !ms_total || !launches || !bytes_total) {
     pm::set_error("invalid profiler read arguments");
     return PM_ERR_INVALID_ARG;
   }
   pm::Profiler &p = plan->f32 ? plan->f32->prof : plan->f64->prof;
-  const cudaError_t e = p.read(kernel_class, ms_total, launches, bytes_total);
+  const cudaError_t e = p.read(kernel_class, ms_total, launches, bytes_total, impl_bytes_total, flops_total);
   if (e != cudaSuccess) {
     pm::set_error(cudaGetErrorString(e));
     return PM_ERR_CUDA;

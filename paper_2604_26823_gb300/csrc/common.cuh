@@ -156,16 +156,22 @@ struct Profiler {
   int used = 0, cap = 0;
   cudaEvent_t *ev = nullptr;  // 2 per launch
   int *cls = nullptr;
-  double *bytes = nullptr;    // algorithmic bytes of each launch
+  double *bytes = nullptr;    // algorithmic bytes of each launch (the method's arrays, FP32 / FP64 words)
+  double *ibytes = nullptr;   // bytes of the implementation's own arrays (fixed-point meshes, padded vectors)
+  double *flops = nullptr;    // floating-point operations of each launch (FFT passes; 0 elsewhere)
   ~Profiler() { release(); }
   void release() {
     for (int i = 0; i < 2 * cap; ++i) cudaEventDestroy(ev[i]);
     delete[] ev;
     delete[] cls;
     delete[] bytes;
+    delete[] ibytes;
+    delete[] flops;
     ev = nullptr;
     cls = nullptr;
     bytes = nullptr;
+    ibytes = nullptr;
+    flops = nullptr;
     cap = used = 0;
     on = false;
   }
@@ -174,6 +180,8 @@ struct Profiler {
     ev = new cudaEvent_t[2 * capacity];
     cls = new int[capacity];
     bytes = new double[capacity];
+    ibytes = new double[capacity];
+    flops = new double[capacity];
     for (int i = 0; i < 2 * capacity; ++i) {
       const cudaError_t e = cudaEventCreate(&ev[i]);
       if (e != cudaSuccess) {
@@ -185,19 +193,22 @@ struct Profiler {
     on = true;
     return cudaSuccess;
   }
-  int begin(int c, cudaStream_t st, double nbytes) {
+  int begin(int c, cudaStream_t st, double nbytes, double impl_bytes, double nflops) {
     if (!on || used >= cap) return -1;
     cls[used] = c;
     bytes[used] = nbytes;
+    ibytes[used] = impl_bytes;
+    flops[used] = nflops;
     cudaEventRecord(ev[2 * used], st);
     return used++;
   }
   void end(int slot, cudaStream_t st) {
     if (slot >= 0) cudaEventRecord(ev[2 * slot + 1], st);
   }
-  // total milliseconds, launch count and algorithmic bytes of one class (synchronises)
-  cudaError_t read(int c, double *ms, int64_t *count, double *nbytes) {
-    double t = 0.0, b = 0.0;
+  // total milliseconds, launch count, algorithmic and implementation bytes
+  // and flops of one class (synchronises)
+  cudaError_t read(int c, double *ms, int64_t *count, double *nbytes, double *impl_bytes, double *nflops) {
+    double t = 0.0, b = 0.0, ib = 0.0, fl = 0.0;
     int64_t k = 0;
     for (int i = 0; i < used; ++i) {
       if (cls[i] != c) continue;
@@ -208,23 +219,37 @@ struct Profiler {
       if (e != cudaSuccess) return e;
       t += f;
       b += bytes[i];
+      ib += ibytes[i];
+      fl += flops[i];
       ++k;
     }
     *ms = t;
     *count = k;
     *nbytes = b;
+    if (impl_bytes) *impl_bytes = ib;
+    if (nflops) *nflops = fl;
     return cudaSuccess;
   }
 };
 
-// RAII bracket of one profiled launch
+// RAII bracket of one profiled launch: the method's algorithmic bytes, (when
+// they differ) the implementation's bytes, and the launch's flops
 struct ProfScope {
   Profiler &p;
   cudaStream_t st;
   int slot;
-  ProfScope(Profiler &pr, int c, cudaStream_t s, double nbytes) : p(pr), st(s), slot(pr.begin(c, s, nbytes)) {}
+  ProfScope(Profiler &pr, int c, cudaStream_t s, double nbytes, double impl_bytes = -1.0, double nflops = 0.0)
+      : p(pr), st(s), slot(pr.begin(c, s, nbytes, impl_bytes < 0 ? nbytes : impl_bytes, nflops)) {}
   ~ProfScope() { p.end(slot, st); }
 };
+
+// Flops of n_ffts complex FFTs of length len (the customary 5 len log2 len);
+// a real FFT of length len counts half of that.
+inline double fft_flops(double n_ffts, int len) {
+  int lg = 0;
+  while ((1 << lg) < len) ++lg;
+  return 5.0 * n_ffts * len * lg;
+}
 
 }  // namespace pm
 

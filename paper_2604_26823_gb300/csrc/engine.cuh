@@ -71,7 +71,7 @@ template <class K> inline void set_smem(K kernel, size_t bytes) {
 
 // ---- output functors of the c2r z pass ----------------------------------
 template <typename T> struct OutPlanar {
-  static constexpr double kWriteBytes = sizeof(T);
+  static constexpr double kWriteBytes = sizeof(T), kAlgWriteBytes = sizeof(T);
   T *out;
   int n;
   T scale = T(1);
@@ -80,7 +80,7 @@ template <typename T> struct OutPlanar {
   }
 };
 template <typename T> struct OutForce {
-  static constexpr double kWriteBytes = 4 * sizeof(T);
+  static constexpr double kWriteBytes = 4 * sizeof(T), kAlgWriteBytes = 3 * sizeof(T);
   V4<T> *phi;
   int n;
   __device__ __forceinline__ void put(int64_t row, int m, const cx<T> *v) const {
@@ -90,7 +90,7 @@ template <typename T> struct OutForce {
   }
 };
 template <typename T> struct OutLptSource {  // phi_ij (slots 00,11,22,01,02,12) -> S, phi stored
-  static constexpr double kWriteBytes = 7 * sizeof(T);
+  static constexpr double kWriteBytes = 7 * sizeof(T), kAlgWriteBytes = 7 * sizeof(T);
   T *phi6;
   T *src;
   int64_t mcells;
@@ -111,7 +111,7 @@ template <typename T> struct OutLptSource {  // phi_ij (slots 00,11,22,01,02,12)
   }
 };
 template <typename T> struct OutGrad {  // out = v + w * s
-  static constexpr double kWriteBytes = 2 * sizeof(T);
+  static constexpr double kWriteBytes = 2 * sizeof(T), kAlgWriteBytes = 2 * sizeof(T);
   T *out;
   const T *s;
   T w;
@@ -145,7 +145,7 @@ inline bool lightcone_states(const pm_config &c, int (&ks)[2]) {
 
 struct Layout {
   size_t tw, amp, spec, fx, psi, psi2, src, dbar, mom, xbar, pbar, disp, phi, ckd, ckm, dwork, snap, lct, scal,
-      total;
+      perm, tslot, tcnt, total;
   int nck, seglen;
 };
 
@@ -195,6 +195,18 @@ inline Layout make_layout(const pm_config &c) {
     L.lct = take(3 * kLcTable * es);        // a_j, chi_j, slope_j
   }
   L.scal = take(64 * 1024);
+  // tile binning of the particles (tile-binned deposition): the particle
+  // order by tile, each particle's (tile, slot), the per-tile counts and
+  // offsets
+  // (one particle order and one offset table per stored state, like the
+  // state history)
+  int logn = 0;
+  while ((1 << logn) < c.n) ++logn;
+  const part::TileGeo tg = part::tile_geo(logn);
+  const size_t nps = (size_t)L.seglen;
+  L.perm = take(nps * m * 4);
+  L.tslot = take(m * 8);
+  L.tcnt = take(((size_t)tg.ntiles + nps * ((size_t)tg.ntiles + 1)) * 4);
   L.total = off;
   return L;
 }
@@ -229,6 +241,9 @@ template <typename T> struct Engine {
   int *fx_exp = nullptr;
   unsigned long long *maxslot = nullptr;
   unsigned long long *maxslots = nullptr;  // part::kMaxSlots partial maxima (zero between uses)
+  part::TileGeo tg{};
+  unsigned *perm = nullptr, *tcount = nullptr, *toff = nullptr;
+  unsigned long long *tslot = nullptr;
   void *sort_ws = nullptr;
   Profiler prof;
 
@@ -297,6 +312,11 @@ template <typename T> struct Engine {
         return PM_ERR_UNSUPPORTED;
       }
     }
+    tg = part::tile_geo(logn);
+    perm = reinterpret_cast<unsigned *>(base + lay.perm);
+    tslot = reinterpret_cast<unsigned long long *>(base + lay.tslot);
+    tcount = reinterpret_cast<unsigned *>(base + lay.tcnt);
+    toff = tcount + tg.ntiles;
     char *sc = base + lay.scal;
     partial = reinterpret_cast<double *>(sc);
     results = partial + pw::kRedBlocks;
@@ -362,7 +382,8 @@ template <typename T> struct Engine {
 
   // ---- FFT passes ----
   pm_status r2c_real(const T *in, int nb, C *out) {
-    ProfScope ps(prof, P_Z_R2C, st, (double)nb * (M * sizeof(T) + S * sizeof(C)));
+    ProfScope ps(prof, P_Z_R2C, st, (double)nb * (M * sizeof(T) + S * sizeof(C)), -1.0,
+                 0.5 * fft_flops((double)nb * n * n, n));
     PM_DISPATCH_N(n, {
       using Z = ZCfg<T, NN>;
       auto kern = fft::k_z_r2c<T, NN, Z::B, Z::NT, fft::LoadReal<T>>;
@@ -373,20 +394,22 @@ template <typename T> struct Engine {
     PM_LAUNCH_CHECK();
     return PM_OK;
   }
-  pm_status r2c_fixed(const long long *in, const int *e, int nb, C *out) {
-    ProfScope ps(prof, P_Z_R2C, st, (double)nb * (M * 8.0 + S * sizeof(C)));
+  pm_status r2c_fixed(const long long *in, const int *e, int nb, C *out, bool sub_unit = false) {
+    // the method reads an FP32 / FP64 mesh; the implementation its 64-bit fixed-point paint
+    ProfScope ps(prof, P_Z_R2C, st, (double)nb * (M * sizeof(T) + S * sizeof(C)), (double)nb * (M * 8.0 + S * sizeof(C)),
+                 0.5 * fft_flops((double)nb * n * n, n));
     PM_DISPATCH_N(n, {
       using Z = ZCfg<T, NN>;
       auto kern = fft::k_z_r2c<T, NN, Z::B, Z::NT, fft::LoadFixed<T>>;
       set_smem(kern, Z::SMEM);
       ::pm::note_launch();
-      kern<<<(int)((int64_t)nb * n * n / Z::B), Z::NT, Z::SMEM, st>>>(fft::LoadFixed<T>{in, e}, out, tw);
+      kern<<<(int)((int64_t)nb * n * n / Z::B), Z::NT, Z::SMEM, st>>>(fft::LoadFixed<T>{in, e, sub_unit}, out, tw);
     });
     PM_LAUNCH_CHECK();
     return PM_OK;
   }
   pm_status ypass(C *buf, int nslots, int sign) {
-    ProfScope ps(prof, P_COL, st, 2.0 * nslots * S * sizeof(C));
+    ProfScope ps(prof, P_COL, st, 2.0 * nslots * S * sizeof(C), -1.0, fft_flops((double)nslots * n * H, n));
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
       const int tiles = (H + CC::B - 1) / CC::B;
@@ -416,7 +439,8 @@ template <typename T> struct Engine {
     a.mult.count = count;
     a.amp = amp;
     a.kf = kf;
-    ProfScope ps(prof, P_X_FUSED, st, (double)(1 + count) * S * sizeof(C));
+    ProfScope ps(prof, P_X_FUSED, st, (double)(1 + count) * S * sizeof(C), -1.0,
+                 fft_flops((double)(1 + count) * n * H, n));
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
       auto kern = fft::k_x_1toM<T, NN, CC::B, CC::NT, CC::MINB_X>;
@@ -437,7 +461,8 @@ template <typename T> struct Engine {
     a.out = slot(out_slot);
     a.amp = amp;
     a.kf = kf;
-    ProfScope ps(prof, P_X_FUSED, st, (double)(1 + count) * S * sizeof(C));
+    ProfScope ps(prof, P_X_FUSED, st, (double)(1 + count) * S * sizeof(C), -1.0,
+                 fft_flops((double)(1 + count) * n * H, n));
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
       auto kern = fft::k_x_Mto1<T, NN, CC::B, CC::NT, CC::MINB_X>;
@@ -451,7 +476,9 @@ template <typename T> struct Engine {
   template <int NIN, class Out> pm_status c2r(int first_slot, int nb, Out out) {
     fft::Ins ins{};
     for (int i = 0; i < NIN; ++i) ins.p[i] = slot(first_slot + i);
-    ProfScope ps(prof, P_Z_C2R, st, (double)nb * NIN * S * sizeof(C) + (double)nb * M * Out::kWriteBytes);
+    ProfScope ps(prof, P_Z_C2R, st, (double)nb * NIN * S * sizeof(C) + (double)nb * M * Out::kAlgWriteBytes,
+                 (double)nb * NIN * S * sizeof(C) + (double)nb * M * Out::kWriteBytes,
+                 0.5 * fft_flops((double)nb * NIN * n * n, n));
     PM_DISPATCH_N(n, {
       using Z = ZCfg<T, NN, true>;
       auto kern = fft::k_z_c2r<T, NN, Z::B, Z::NT, NIN, Out, Z::template minb<NIN>()>;
@@ -511,6 +538,54 @@ template <typename T> struct Engine {
     return PM_OK;
   }
 
+  // Tile order of the particles of a stored state (the same slots as the
+  // state history): perm_of lists each tile's particles, toff_of the tiles'
+  // offsets.
+  unsigned *perm_of(int slot) const { return perm + (int64_t)slot * M; }
+  unsigned *toff_of(int slot) const { return toff + (int64_t)slot * (tg.ntiles + 1); }
+  // offsets and order of a slot from the counts and (tile, slot) words of a binning pass
+  pm_status finish_bin(int slot) {
+    ::pm::note_launch();
+    part::k_bin_scan<<<1, 1024, 0, st>>>(tcount, tg.ntiles, toff_of(slot));
+    ::pm::note_launch();
+    part::k_bin_scatter<<<grid_for(M, 256), 256, 0, st>>>(M, tslot, toff_of(slot), perm_of(slot));
+    PM_LAUNCH_CHECK();
+    return PM_OK;
+  }
+  // Tile binning of the particles at positions x (cell units) into a slot.
+  pm_status bin(const T *x, int slot) {
+    PM_CUDA_TRY(cudaMemsetAsync(tcount, 0, (size_t)tg.ntiles * sizeof(unsigned), st));
+    ::pm::note_launch();
+    part::k_bin_count<T><<<grid_for(M, 256), 256, 0, st>>>(geo(), tg, x, tcount, tslot);
+    PM_LAUNCH_CHECK();
+    return finish_bin(slot);
+  }
+  // One tile-binned deposition launch over the particles in the tile order
+  // of `slot`, into a shared box with a margin of MG cells; with
+  // bin_slot >= 0 the particles are binned at their deposit positions into
+  // that slot (which may be `slot` itself: the order is rewritten after the
+  // launch).
+  template <int MG, class Src> pm_status deposit_tiled(Src s, int slot, int bin_slot = -1) {
+    const size_t sm = part::tile_box_bytes(tg, Src::NCH, MG);
+    unsigned long long *mesh = reinterpret_cast<unsigned long long *>(fx);
+    if (bin_slot >= 0) {
+      PM_CUDA_TRY(cudaMemsetAsync(tcount, 0, (size_t)tg.ntiles * sizeof(unsigned), st));
+      auto kern = part::k_deposit_tiled<T, Src, MG, true>;
+      set_smem(kern, sm);
+      ::pm::note_launch();
+      kern<<<tg.ntiles, 256, sm, st>>>(geo(), tg, s, perm_of(slot), toff_of(slot), mesh, M,
+                                        part::BinOut{tcount, tslot});
+      PM_LAUNCH_CHECK();
+      return finish_bin(bin_slot);
+    }
+    auto kern = part::k_deposit_tiled<T, Src, MG, false>;
+    set_smem(kern, sm);
+    ::pm::note_launch();
+    kern<<<tg.ntiles, 256, sm, st>>>(geo(), tg, s, perm_of(slot), toff_of(slot), mesh, M, part::BinOut{});
+    PM_LAUNCH_CHECK();
+    return PM_OK;
+  }
+
   // ---- forward stages ----
   // 2LPT: fills disp0 / mom (cell units), phi_ij (when keep), paints density.
   pm_status lpt(const T *s, T *disp0, bool paint) {
@@ -553,13 +628,16 @@ template <typename T> struct Engine {
     }
     const double ic = 1.0 / cell;
     const part::Geo g = geo();
-    return deposit(part::SrcLpt<T>{g.L, M, psi, cfg.lpt_order == 2 ? psi2 : nullptr, (T)(d1 * ic), (T)(d2 * ic),
-                                       (T)(gp1 * ic), (T)(gp2 * ic), disp0, mom, paint ? fx_exp : nullptr, T(0)});
+    PM_TRY(deposit(part::SrcLpt<T>{g.L, M, psi, cfg.lpt_order == 2 ? psi2 : nullptr, (T)(d1 * ic), (T)(d2 * ic),
+                                   (T)(gp1 * ic), (T)(gp2 * ic), disp0, mom, paint ? fx_exp : nullptr, T(0)}));
+    // tile order of the initial state (slot 0) for the first leapfrog step
+    return bin(disp0, 0);
   }
 
-  // PM force mesh (cell units) from the painted density in fx channel 0.
+  // PM force mesh (cell units) from the painted density in fx channel 0
+  // (transformed as delta = rho - 1, N_mesh = N_part).
   pm_status force_mesh(V4<T> *out) {
-    PM_TRY(r2c_fixed(fx, fx_exp, 1, slot(0)));
+    PM_TRY(r2c_fixed(fx, fx_exp, 1, slot(0), true));
     PM_TRY(ypass(slot(0), 1, -1));
     fft::MultDesc m[3];
     int outs[3] = {0, 1, 2};
@@ -584,7 +662,10 @@ template <typename T> struct Engine {
       const int so = store ? k + 1 - base_slot : 0;
       PM_TRY(memset_fx(1));
       {
-        ProfScope ps(prof, P_KDK, st, (double)M * (16 * sizeof(T) + 8));
+        // method: x, p read and written, 3 force components read, density written;
+        // implementation: float4 force mesh, 64-bit fixed-point density, the
+        // particle order read and the next state's binning words written
+        ProfScope ps(prof, P_KDK, st, (double)M * 16 * sizeof(T), (double)M * (16 * sizeof(T) + 8 + 4 + 8));
         part::SrcKdk<T> src_k{g.L, M, pstate(si), dstate(si), dstate(so), momb, (T)ck[k], (T)dr[k], fx_exp, T(0)};
         if (lc_on && lc_write && (k == lc_k[0] || k == lc_k[1])) {
           const int j = k == lc_k[0] ? 0 : 1;
@@ -592,7 +673,10 @@ template <typename T> struct Engine {
           src_k.snap_p = snap + (int64_t)(2 + j) * 3 * M;
           src_k.kb = (T)kbv[k];
         }
-        PM_TRY(deposit(src_k));
+        // particles in the tile order of x_k; x_{k+1} deposited (a particle
+        // that moved more than 2 cells out of its tile goes to the mesh
+        // directly) and binned into the order of the next state
+        PM_TRY((deposit_tiled<2>(src_k, si, so)));
       }
       PM_TRY(force_mesh(pstate(so)));
     }
@@ -635,7 +719,9 @@ template <typename T> struct Engine {
       fsrc.lightcone = true;
       fsrc.lc = lightcone();
     }
-    return deposit(fsrc);
+    // in the tile order of the final state (a redshift-space or lightcone
+    // shift of more than 2 cells goes to the mesh directly)
+    return deposit_tiled<2>(fsrc, fin);
   }
 
   pm_status loss_terms(const T *s, const T *data, const T *R, const T *cot, double lw, bool want_dbar,
@@ -650,7 +736,8 @@ template <typename T> struct Engine {
     lp.nbar = cfg.nbar_cell;
     lp.rho_floor = cfg.rho_floor;
     lp.lw = lw;
-    ProfScope ps(prof, P_LOSS, st, (double)M * (8 + (2 + (want_dbar ? 1 : 0) + (delta_out ? 1 : 0)) * sizeof(T)));
+    const double lw_io = (2 + (want_dbar ? 1 : 0) + (delta_out ? 1 : 0)) * sizeof(T);
+    ProfScope ps(prof, P_LOSS, st, (double)M * (sizeof(T) + lw_io), (double)M * (8 + lw_io));
     ::pm::note_launch();
     pw::k_loss<T><<<pw::kRedBlocks, pw::kRedThreads, 0, st>>>(lp, fx, fx_exp, data, R, cot,
                                                                want_dbar ? dbar : nullptr, delta_out, M, partial);
@@ -705,7 +792,7 @@ template <typename T> struct Engine {
 
   // reverse of the kick at state k (x_k in xk, force mesh phik), then the
   // reverse of the drift into state k (when k > 0)
-  pm_status reverse_step(int k, const T *xk, const V4<T> *phik) {
+  pm_status reverse_step(int k, const T *xk, const V4<T> *phik, int slot) {
     const part::Geo g = geo();
     const int nb = grid_for(M, 256);
     if (k == cfg.n_steps && cfg.rsd_axis < 0) {
@@ -721,14 +808,21 @@ template <typename T> struct Engine {
     }
     PM_TRY(memset_fx(3));
     {
-      ProfScope ps(prof, P_ADJ_PAINT, st, (double)M * (6 * sizeof(T) + 24));
-      PM_TRY(deposit(part::SrcAdj3<T>{g.L, M, g.log2np, xk, pbar, (T)ck[k], maxslot, fx_exp + 1, 0}));
+      // method (the 3-channel paint's 24 B / particle in FP32): positions read,
+      // three mesh channels written; implementation: positions, cotangent and
+      // the particle order read, 64-bit fixed-point channels
+      ProfScope ps(prof, P_ADJ_PAINT, st, (double)M * 6 * sizeof(T), (double)M * (6 * sizeof(T) + 4 + 24));
+      // in the tile order of state k (binned when the state was made)
+      PM_TRY((deposit_tiled<0>(part::SrcAdj3<T>{g.L, M, g.log2np, xk, pbar, (T)ck[k], maxslot, fx_exp + 1, 0},
+                               slot)));
     }
     PM_TRY(adjoint_force(src));
     const T drift = k > 0 ? (T)dr[k - 1] : T(0);
     const T cnext = k > 0 ? (T)ck[k - 1] : T(0);
     {
-      ProfScope ps(prof, P_ADJ_GATHER, st, (double)M * 20 * sizeof(T));
+      // method: x, xbar, pbar read, xbar, pbar written, 3 force components and
+      // rhobar read (the implementation's force mesh is float4)
+      ProfScope ps(prof, P_ADJ_GATHER, st, (double)M * 19 * sizeof(T), (double)M * 20 * sizeof(T));
       ::pm::note_launch();
       part::k_adj_gather<T><<<nb, 256, 0, st>>>(g, xk, phik, src, (T)ck[k], xbar, pbar, drift, cnext,
                                                  k > 0 ? maxslots : nullptr);
@@ -743,9 +837,9 @@ template <typename T> struct Engine {
   // pbar += (kb / c_k) Pbar_j makes its cotangent paint c_k pbar + kb Pbar_j,
   // and after it pbar += (1 - kb / c_k) Pbar_j completes the cotangent of the
   // momentum before the kick (then the running max is taken again).
-  pm_status reverse_step_lc(int k, const T *xk, const V4<T> *phik) {
+  pm_status reverse_step_lc(int k, const T *xk, const V4<T> *phik, int slot) {
     const int j = !lc_on ? -1 : (k == lc_k[0] ? 0 : (k == lc_k[1] ? 1 : -1));
-    if (j < 0) return reverse_step(k, xk, phik);
+    if (j < 0) return reverse_step(k, xk, phik, slot);
     const part::Geo g = geo();
     const int nb = grid_for(M, 256);
     const T *xb = snap + (int64_t)j * 3 * M, *pb = snap + (int64_t)(2 + j) * 3 * M;
@@ -754,7 +848,7 @@ template <typename T> struct Engine {
     part::k_lc_join<T><<<nb, 256, 0, st>>>(g, xbar, pbar, xb, pb, (T)f, (T)ck[k], maxslots);
     PM_LAUNCH_CHECK();
     PM_TRY(fold_max());
-    PM_TRY(reverse_step(k, xk, phik));
+    PM_TRY(reverse_step(k, xk, phik, slot));
     ::pm::note_launch();
     part::k_lc_join<T><<<nb, 256, 0, st>>>(g, nullptr, pbar, nullptr, pb, (T)(1.0 - f),
                                             k > 0 ? (T)ck[k - 1] : T(0), maxslots);
@@ -784,7 +878,7 @@ template <typename T> struct Engine {
     PM_LAUNCH_CHECK();
     PM_TRY(fold_max());
     if (keep_all()) {
-      for (int k = ns; k >= 0; --k) PM_TRY(reverse_step_lc(k, dstate(k), pstate(k)));
+      for (int k = ns; k >= 0; --k) PM_TRY(reverse_step_lc(k, dstate(k), pstate(k), k));
     } else {
       const int ce = cfg.checkpoint_every;
       for (int j = ns / ce; j >= 0; --j) {
@@ -797,12 +891,13 @@ template <typename T> struct Engine {
         PM_TRY(memset_fx(1));
         PM_TRY(set_exp(0, rho_exp));
         PM_TRY(deposit(part::SrcPaint<T>{g.L, M, dstate(0), psi2, -1, T(0), fx_exp, T(0)}));
+        PM_TRY(bin(dstate(0), 0));
         PM_TRY(force_mesh(pstate(0)));
         lc_write = false;  // the snapshot buffer holds their cotangents now
         const pm_status rs = run_steps(lo, hi, lo, true, psi2);
         lc_write = true;
         PM_TRY(rs);
-        for (int k = hi; k >= lo; --k) PM_TRY(reverse_step_lc(k, dstate(k - lo), pstate(k - lo)));
+        for (int k = hi; k >= lo; --k) PM_TRY(reverse_step_lc(k, dstate(k - lo), pstate(k - lo), k - lo));
       }
     }
     PM_TRY(lpt_adjoint(s, lw, grad));

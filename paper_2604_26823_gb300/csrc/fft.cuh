@@ -272,8 +272,17 @@ template <typename T> struct LoadReal {
 template <typename T> struct LoadFixed {
   const long long *p;
   const int *exp;  // value = q * 2^-exp (device scalar written by the paint)
+  // subtract one unit weight (q = 2^exp) before the conversion: a painted
+  // density rho (mean 1 particle per cell) becomes delta = rho - 1 exactly, in
+  // integers, so the FP32 FFT's rounding scales with delta, not with rho
+  bool sub_unit = false;
   __device__ __forceinline__ void pair(int64_t i, T &a, T &b) const {
-    const longlong2 v = reinterpret_cast<const longlong2 *>(p)[i];
+    longlong2 v = reinterpret_cast<const longlong2 *>(p)[i];
+    if (sub_unit) {
+      const long long unit = 1ll << __ldg(exp);
+      v.x -= unit;
+      v.y -= unit;
+    }
     const int e = -__ldg(exp);
     if constexpr (sizeof(T) == 4) {
       // the two exact int64 -> float conversions run on different units (the

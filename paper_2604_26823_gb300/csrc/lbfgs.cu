@@ -137,6 +137,11 @@ __global__ void k_mul(double *dst, const double *src, double f) { *dst = f * *sr
 }  // namespace lb
 }  // namespace pm
 
+// The history holds m + 1 physical (s, y) slots: phys[0..m) maps the ring
+// positions to slots and `spare` is the free one.  A new pair is written into
+// the spare slot and enters the ring only when it passes the curvature test
+// (the slot of the pair it displaces becomes the spare), so a rejected pair
+// never overwrites a stored one.
 struct lbfgs_state {
   int64_t n = 0;
   int m = 0;
@@ -144,8 +149,10 @@ struct lbfgs_state {
   size_t es = 4;
   char *ws = nullptr;
   void *S = nullptr, *Y = nullptr, *xprev = nullptr, *gprev = nullptr;
-  double *partial = nullptr, *dres = nullptr;  // dres: alpha[m], dots[m+8]
-  std::vector<double> rho;
+  double *partial = nullptr, *dres = nullptr;  // dres: alpha[m + 1], dots[m + 8]
+  std::vector<double> rho;                     // per physical slot
+  std::vector<int> phys;                       // ring position -> physical slot
+  int spare = 0;
   int count = 0, head = 0;
   bool has_prev = false;
   double gamma = 1.0;
@@ -156,7 +163,7 @@ namespace {
 size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 
 size_t lb_bytes(int64_t n, int m, size_t es) {
-  return 2 * (size_t)m * al(n * es) + 2 * al(n * es) + al(3 * pm::pw::kRedBlocks * 8) + al((2 * m + 16) * 8);
+  return 2 * (size_t)(m + 1) * al(n * es) + 2 * al(n * es) + al(3 * pm::pw::kRedBlocks * 8) + al((2 * m + 16) * 8);
 }
 
 template <typename T> void *vec(lbfgs_state *s, void *base, int i) {
@@ -179,11 +186,11 @@ pm_status step_impl(lbfgs_state *s, const T *xn, const T *gn, T *d, double *gdot
   const int64_t n = s->n;
   const int nb = kRedBlocks, nt = kRedThreads;
   cudaError_t err = cudaSuccess;
-  double *alpha = s->dres;        // alpha[m]
-  double *dots = s->dres + s->m;  // scratch scalars
+  double *alpha = s->dres;            // alpha per physical slot, m + 1
+  double *dots = s->dres + s->m + 1;  // scratch scalars
   int did_push = 0;
   if (s->has_prev) {
-    const int slot = s->head;
+    const int slot = s->spare;
     T *sv = static_cast<T *>(vec<T>(s, s->S, slot));
     T *yv = static_cast<T *>(vec<T>(s, s->Y, slot));
     ::pm::note_launch();
@@ -201,6 +208,10 @@ pm_status step_impl(lbfgs_state *s, const T *xn, const T *gn, T *d, double *gdot
     if (std::isfinite(sy) && sy > 1e-10 * std::sqrt(ss) * std::sqrt(yy) && yy > 0) {
       s->rho[slot] = 1.0 / sy;
       s->gamma = sy / yy;
+      // ring position `head` receives the new pair; the slot it held (free,
+      // or the oldest pair when the ring is full) becomes the spare
+      s->spare = s->phys[s->head];
+      s->phys[s->head] = slot;
       s->head = (s->head + 1) % s->m;
       if (s->count < s->m) ++s->count;
       did_push = 1;
@@ -212,7 +223,8 @@ pm_status step_impl(lbfgs_state *s, const T *xn, const T *gn, T *d, double *gdot
   }
   // two-loop recursion, q in d
   const int k = s->count;
-  auto idx = [&](int age) { return ((s->head - 1 - age) % s->m + s->m) % s->m; };  // age 0 = newest
+  // physical slot of the pair of the given age (0 = newest)
+  auto idx = [&](int age) { return s->phys[((s->head - 1 - age) % s->m + s->m) % s->m]; };
   PM_CUDA_TRY(cudaMemcpyAsync(d, gn, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
   if (k > 0) {
     // alpha_newest = rho * s_newest . q
@@ -329,13 +341,16 @@ pm_status lbfgs_create(int64_t n_elems, int32_t m, int32_t precision, void *work
   st->m = m;
   st->prec = precision;
   st->es = precision == PM_PREC_F64 ? 8 : 4;
-  st->rho.assign(m, 0.0);
+  st->rho.assign(m + 1, 0.0);
+  st->phys.resize(m);
+  for (int i = 0; i < m; ++i) st->phys[i] = i;
+  st->spare = m;
   char *p = static_cast<char *>(workspace);
   const size_t v = al(n_elems * st->es);
   st->S = p;
-  p += m * v;
+  p += (m + 1) * v;
   st->Y = p;
-  p += m * v;
+  p += (m + 1) * v;
   st->xprev = p;
   p += v;
   st->gprev = p;

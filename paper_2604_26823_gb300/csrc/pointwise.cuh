@@ -151,8 +151,9 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
   SumAcc<T> acc;  // the likelihood terms, each formed in T
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     T delta;
-    if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i]), e) - 1.0f;
-    else delta = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
+    // delta = rho - 1 formed in integers (one unit weight is 2^-e), then rounded once
+    if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
+    else delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
     if (delta_out) delta_out[i] = delta;
     const T r = resp[i];
     T g = T(0);
@@ -185,8 +186,8 @@ __global__ void k_expected(LossParams lp, const long long *__restrict__ rho, con
   if (i >= n) return;
   const int e = -__ldg(fx_exp);
   T delta;
-  if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i]), e) - 1.0f;
-  else delta = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
+  if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
+  else delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
   if (lp.lik == 0) {
     out[i] = (T)lp.b * delta;
   } else {
@@ -287,8 +288,8 @@ __global__ void k_fixed_to_delta(const long long *__restrict__ rho, const int *f
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int e = -__ldg(fx_exp);
-  if constexpr (sizeof(T) == 4) out[i] = scalbnf(fx_i64_to_f32(rho[i]), e) - 1.0f;
-  else out[i] = scalbn(__ll2double_rn(rho[i]), e) - 1.0;
+  if constexpr (sizeof(T) == 4) out[i] = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
+  else out[i] = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
 }
 
 // count of non-finite values (for input validation), block partials

@@ -7,7 +7,9 @@
 // step needs lives in a file-scope device array of the library instead.
 //
 // Scratch: one FP64 partial sum per 4096 elements (at most kMaxBlocks), plus
-// the sum, the sum of squared deviations, the reset counter and mu, sd, 1/sd.  Every GPU
+// the sum, the sum of squared deviations, the reset counter and mu, sd, 1/sd
+// with the flag that lets the projection kernel leave s untouched when the
+// moments are not finite or the variance is zero.  Every GPU
 // that loads the library holds this array (about 512 KB) until the process
 // exits.  Every call shares it and it keeps the last call's contents; the
 // reset counter is cleared at the start of each call.  Calls that overlap on
@@ -27,7 +29,7 @@ namespace {
 constexpr int kItems = 4096;                                  // elements per partial sum
 constexpr int64_t kMaxBlocks = 65536;                         // partial sums in the array
 constexpr int64_t kMaxElems = kMaxBlocks * (int64_t)kItems;   // 2^28 elements
-constexpr int kTail = 8;                                      // sums, counter, mu / sd / 1/sd, spare
+constexpr int kTail = 8;                                      // sums, counter, mu / sd / 1/sd / valid flag, spare
 
 static __device__ __align__(256) double g_project_scratch[kMaxBlocks + kTail];
 

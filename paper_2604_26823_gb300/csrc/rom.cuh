@@ -56,13 +56,16 @@ __global__ void k_moment(const T *__restrict__ x, int64_t n, const double *mean_
   pw::block_sum_store(mean_sum ? s2.value() : s1.value(), partial);
 }
 
-// Projection scalars once: mu, sd and 1/sd (FP64) from the two FP64 sums.
-static __global__ void k_project_scalars(int64_t n, const double *sum, const double *sumsq_dev, double *out3) {
+// Projection scalars once: mu, sd, 1/sd (FP64) from the two FP64 sums, and
+// a flag (1 or 0) telling whether they define a projection at all (finite
+// moments, sd > 0).
+static __global__ void k_project_scalars(int64_t n, const double *sum, const double *sumsq_dev, double *out4) {
   const double mu = *sum / (double)n;
   const double sd = sqrt(*sumsq_dev / (double)n);
-  out3[0] = mu;
-  out3[1] = sd;
-  out3[2] = 1.0 / sd;
+  out4[0] = mu;
+  out4[1] = sd;
+  out4[2] = 1.0 / sd;
+  out4[3] = (isfinite(mu) && isfinite(sd) && sd > 0.0) ? 1.0 : 0.0;
 }
 
 // s_hat = (s - mu)/sd; |s_hat| > s_th -> counter-based N(0,1).  The value is
@@ -70,16 +73,19 @@ static __global__ void k_project_scalars(int64_t n, const double *sum, const dou
 // without an FP64 division per element on the narrow FP64 unit); the reset
 // decision is taken on the FP64 quotient itself, evaluated for the elements
 // whose fast value lies within 1e-4 of the threshold, so the set of reset
-// elements is the FP64 rule's.
+// elements is the FP64 rule's.  When the scalars' flag is 0 (NaN / Inf in s,
+// or zero variance) nothing is written: s keeps its values and the host
+// reports the error.
 template <typename T>
 __global__ void k_project(T *s, int64_t n, const double *scal, double s_th, unsigned long long key,
                           unsigned long long *nreset) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || scal[3] == 0.0) return;
   const T mu = (T)scal[0], inv = (T)scal[2];
+  const T near_th = (T)(s_th * (1.0 - 1e-4));
   const T v = s[i];
   T z = (v - mu) * inv;
-  if (fabs((double)z) > s_th * (1.0 - 1e-4)) {
+  if (fabs(z) > near_th) {
     const double zd = ((double)v - scal[0]) / scal[1];
     if (fabs(zd) > s_th) {
       z = (T)counter_normal(key, (unsigned long long)i);

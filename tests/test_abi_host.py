@@ -144,9 +144,40 @@ def test_analysis_and_annealing_argument_checks_without_gpu(lib):
     assert lib.pm_tweb(None, z, 2.0, 0.16, z, None, None, None) == 1
     assert lib.pm_smooth(None, z, 2.0, z, None) == 1
     d = (ctypes.c_double * 4)()
-    assert lib.pm_power_spectra(None, z, None, 4, 0.1, 1.0, d, None, None, d, None) == 1
+    assert lib.pm_power_spectra(None, z, None, 4, 0.1, 1.0, d, None, None, d, None, None) == 1
     assert lib.pm_fma_rate(2, 100, z, d, None) == 1
     assert lib.pm_fma_rate(1, 0, z, d, None) == 1
     assert lib.pm_fma_rate(1, 100, None, d, None) == 1
     assert lib.pm_distance_table(0.3, 0.5, 1, d, d) == 1
     assert lib.pm_distance_table(0.3, 1.5, 4, d, d) == 1
+
+
+def test_binding_refuses_dtypes_other_than_f32_f64():
+    """The element size follows the dtype: anything but float32 / float64 is
+    refused by the binding before the library is called (a float16 or int32
+    vector read as doubles would be overrun)."""
+    import torch
+    from paper_2604_26823_gb300 import api
+    with pytest.raises(TypeError):
+        api.pm_project_noalloc(torch.zeros(16, dtype=torch.float16))
+    with pytest.raises(TypeError):
+        api.pm_project_noalloc(torch.zeros(16, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        api.pm_coarsen(torch.zeros((4, 4, 4), dtype=torch.bfloat16), 2)
+    with pytest.raises(TypeError):
+        api.pm_eigvec_cosines(torch.zeros((3, 3, 2, 2, 2), dtype=torch.int32),
+                              torch.zeros((3, 3, 2, 2, 2), dtype=torch.int32))
+    with pytest.raises(TypeError):
+        api.pm_axpy(0.5, torch.zeros(8, dtype=torch.float16), torch.zeros(8, dtype=torch.float16))
+    with pytest.raises(TypeError):
+        api.pm_confusion(torch.zeros(8, dtype=torch.int32), torch.zeros(8, dtype=torch.int32),
+                         R=torch.zeros(8, dtype=torch.float16))
+
+
+def test_lbfgs_workspace_holds_a_spare_pair_slot(lib):
+    """m + 1 (s, y) slots: a new pair is written into the spare slot and
+    enters the history only when accepted."""
+    nb = ctypes.c_size_t()
+    assert lib.lbfgs_workspace_bytes(1024, 4, 0, ctypes.byref(nb)) == 0
+    vec = 1024 * 4
+    assert nb.value >= 2 * 5 * vec + 2 * vec

@@ -15,8 +15,9 @@ the particles sitting that close to a face, and the gradient changes by
 O(sqrt(position error)).  For noise-dominated adjoints (the Poisson
 likelihood, ten steps with RSD) this exceeds 1e-4 for ANY FP32 evaluation:
 the oracle itself, run with single-precision library FFTs, misses it by the
-same margin.  The FP32 bound is therefore max(1e-4, 3 x the error of that
-independent FP32 evaluation), with cosine >= 0.99999 always.
+same margin.  The FP32 bound is therefore 1e-4 on every case where that
+independent FP32 evaluation meets 1e-4, and 1.5 x its error on the others,
+with cosine >= 0.99999 always; each case prints both errors.
 """
 import numpy as np
 import pytest
@@ -66,6 +67,7 @@ def test_linear_field(api, name, prec):
     got = api.pm_linear_field(plan, dev(s, prec)).cpu().numpy()
     lnk, lnp = table()
     ref = OM.linear_field(s, oracle_config(CASES[name]), lnk, lnp)
+    print(f"linear field {name} {prec}: rel L2 {rel_l2(got, ref):.2e}")
     assert rel_l2(got, ref) < TOL[prec] * 0.1
 
 
@@ -94,6 +96,8 @@ def test_force_and_density(api, name, prec):
     cfg = oracle_config(kw)
     lnk, lnp = table()
     rf, _, rdelta = OM.force(disp.T, cfg, OM._Ops(cfg, lnk, lnp))
+    print(f"force {name} {prec}: density rel L2 {rel_l2(dens.cpu().numpy(), rdelta):.2e}, "
+          f"force {rel_l2(f.cpu().numpy(), rf.T):.2e}")
     assert rel_l2(dens.cpu().numpy(), rdelta) < TOL[prec]
     assert rel_l2(f.cpu().numpy(), rf.T) < TOL[prec]
     # momentum conservation survives the FP32 kernels: sum_p F_p ~ 0
@@ -108,6 +112,8 @@ def test_evolve(api, name, prec):
     s, _, _ = case_inputs(name)
     disp, mom = api.pm_evolve(plan, dev(s, prec))
     rd, rm = oracle_evolve(name)
+    print(f"evolve {name} {prec}: displacement rel L2 {rel_l2(disp.cpu().numpy(), rd.T):.2e}, "
+          f"momentum {rel_l2(mom.cpu().numpy(), rm.T):.2e}")
     assert rel_l2(disp.cpu().numpy(), rd.T) < 3 * TOL[prec]
     assert rel_l2(mom.cpu().numpy(), rm.T) < 3 * TOL[prec]
 
@@ -136,11 +142,19 @@ def test_gradient(api, name, prec):
     rloss, rg, _ = oracle_gradient(name)
     g = g.cpu().numpy()
     assert abs(loss - rloss) < TOL[prec] * abs(rloss)
+    err, cos = rel_l2(g, rg), cosine(g, rg)
     bound = GTOL[prec]
     if prec == "f32":
-        bound = max(bound, 3.0 * rel_l2(oracle_gradient_single_fft(name)[1], rg))
-    assert rel_l2(g, rg) < bound, (rel_l2(g, rg), bound)
-    assert cosine(g, rg) > 1 - (1e-5 if prec == "f32" else 1e-12)
+        g1 = oracle_gradient_single_fft(name)[1]
+        e1, c1 = rel_l2(g1, rg), cosine(g1, rg)
+        if e1 >= GTOL["f32"]:
+            bound = 1.5 * e1
+        print(f"gradient {name} f32: GPU rel L2 {err:.3e} cos {cos:.9f}; single-precision-FFT oracle "
+              f"rel L2 {e1:.3e} cos {c1:.9f}; bound {bound:.3e}")
+    else:
+        print(f"gradient {name} f64: GPU rel L2 {err:.3e} cos {cos:.12f}")
+    assert err < bound, (err, bound)
+    assert cos > 1 - (1e-5 if prec == "f32" else 1e-12)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
@@ -201,6 +215,7 @@ def test_fd_directions_fp64_gpu(api):
         fd = (fp - fm) / 2e-3
         gu = float((g * u).sum())
         errs.append(abs(fd - gu) / (abs(gu) + 1e-3 * float(g.norm())))
+    print("FD along 16 directions, FP64 GPU path, 128^3 RSD: median %.2e max %.2e" % (np.median(errs), max(errs)))
     assert np.median(errs) < 1e-4 and max(errs) < 1e-2, errs
 
 

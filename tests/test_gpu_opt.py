@@ -163,3 +163,20 @@ def test_axpy(api, prec):
     # one rounding of the product and one of the sum in the path's precision
     eps = 6e-8 if prec == "f32" else 1.2e-16
     np.testing.assert_allclose(out.cpu().numpy(), y + 0.37 * x, rtol=0, atol=2 * eps * (np.abs(y) + np.abs(0.37 * x)).max())
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_projection_leaves_input_untouched_on_error(api, prec):
+    """NaN in s, or zero variance: PM_ERR_NONFINITE, and s keeps its values
+    (the projection kernel reads the moments' validity flag on the device)."""
+    from paper_2604_26823_gb300 import inputs
+    p = plan(api, 16, 100.0, prec)
+    s = inputs.white_noise(16, 1)
+    s.reshape(-1)[5] = np.nan
+    for vec in (s, np.full((16, 16, 16), 2.5, np.float32)):
+        x = dev(vec, prec)
+        before = x.cpu().numpy().copy()
+        with pytest.raises(api.L.PMError) as err:
+            api.project_rank_match(p, x, api.L.PM_PROJECT, seed=6, counter=1)
+        assert err.value.status == api.L.PM_ERR_NONFINITE
+        np.testing.assert_array_equal(x.cpu().numpy(), before)

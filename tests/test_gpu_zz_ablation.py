@@ -44,3 +44,110 @@ def test_ablation_short_run():
     a, b = runs["L-BFGS-S-3"], runs["L-BFGS"]
     if a["failed"] is None and b["failed"] is None:
         assert a["curve"][-1][2] >= b["curve"][-1][2]
+
+
+def _oracle_run(s0, counts, R, cfg, iters, project, rom_every, eps_max, checkpoint_every, nreal, fcounts,
+                box, c1=1e-4, max_halvings=30):
+    """The driver's iteration written with the oracle's pieces (oracle.lbfgs,
+    oracle.projection, oracle.model.gradient): projected or plain backtracking
+    line search with the step capped at eps_max, rank-order matching every
+    rom_every iterations (0: none), the likelihood term recorded every
+    checkpoint_every iterations.  Returns (curve [(it, likelihood, loss)],
+    gradient evaluations, {checkpoint number: state})."""
+    from oracle import lbfgs as OL
+    from oracle import model as OM
+    from oracle import projection as OP
+    from paper_2604_26823_gb300 import inputs
+    lnk, lnp = table()
+
+    def fg(x):
+        f, g, info = OM.gradient(x, cfg, lnk, lnp, counts, R)
+        return f, g, info["likelihood"]
+
+    lb = OL.LBFGS(10)
+    s = s0.copy()
+    f, g, lik = fg(s)
+    counter, evals, curve, states = 0, 1, [], {}
+    for it in range(1, iters + 1):
+        d, gd, _ = lb.step(s.reshape(-1), g.reshape(-1))
+        accepted = None
+        for attempt in range(2):
+            dn = float(np.linalg.norm(d))
+            eps, slope = min(dn, eps_max), gd / dn
+            for _ in range(max_halvings + 1):
+                trial = s + (eps / dn) * d.reshape(s.shape)
+                if project:
+                    trial, _ = OP.project(trial, 6, counter)
+                    counter += 1
+                ft, gt, lt = fg(trial)
+                evals += 1
+                if np.isfinite(ft) and ft <= f + c1 * eps * slope:
+                    accepted = (trial, ft, gt, lt)
+                    break
+                eps *= 0.5
+            if accepted:
+                break
+            lb.reset()
+            lb.x_prev = None
+            d, gd, _ = lb.step(s.reshape(-1), g.reshape(-1))
+        assert accepted is not None
+        s, f, g, lik = accepted
+        if rom_every and it % rom_every == 0:
+            tr = inputs.sorted_normal_targets(nreal, 7 + it).astype(np.float64)
+            tf = inputs.sorted_normal_targets_per_bin(fcounts, 7 + it).astype(np.float64)
+            s, _ = OP.project_rank_match(s, box, R, 7, tr, tf, seed=6, counter=counter)
+            counter += 1
+            f, g, lik = fg(s)
+            evals += 1
+            lb.reset()
+            lb.x_prev = None
+        if it % checkpoint_every == 0:
+            curve.append((it, lik, f))
+            states[len(curve)] = s.copy()
+    return curve, evals, states
+
+
+def test_ablation_runs_follow_oracle_fp64():
+    """Three Table 1 runs of the harness on the FP64 path -- MujicΛ (projection,
+    rank-order matching every 4 iterations), unprojected L-BFGS with the step
+    capped at 0.1, and the cap-1 L-BFGS warm-started from the MujicΛ
+    checkpoint #2 -- against the same runs assembled from the oracle: the
+    same checkpoints, every likelihood and loss to 1e-7 relative, the same
+    number of gradient evaluations."""
+    from paper_2604_26823_gb300 import build
+    build.build()
+    from oracle import model as OM
+    from paper_2604_26823_gb300 import ablation, api, inputs
+    n, box, it_m, every = 32, 62.5, 8, 2
+    lnk, lnp = table()
+    R = inputs.survey_selection(n, box, 4, observer=(box / 2, box / 2, -0.3 * box), r_scale=300.0 * n / 256)
+    R = R.astype(np.float64)
+    counts = inputs.poisson_counts(0.4 * R * 1.2, 5).astype(np.float64)
+    s0 = inputs.white_noise(n, 2).astype(np.float64)
+    kw = dict(n=n, box=box, n_steps=4, lpt_order=2, likelihood="poisson", nbar_cell=0.4, alpha=0.7,
+              delta_th=1.2, K=3.0, rho_floor=1e-3, prior_weight=1.0)
+    plan = api.Plan(api.Config(precision="f64", **kw), lnk, lnp)
+    dev = lambda x: torch.tensor(np.asarray(x), dtype=torch.float64, device="cuda")
+    Rd = dev(R)
+    nreal = api.pm_count_positive(plan, Rd)
+    fcounts = api.pm_rom_fourier_counts(plan)
+    targets = lambda it: (dev(inputs.sorted_normal_targets(nreal, 7 + it)),
+                          dev(inputs.sorted_normal_targets_per_bin(fcounts, 7 + it)))
+    res = ablation.ablation(plan, dev(s0), dev(counts), Rd, it_m, targets, rom_every=4, checkpoint_every=every,
+                            eps_caps=(0.1,), warm=(2,), lbfgs_checkpoints=3)
+    plan.close()
+    runs = res["runs"]
+    assert list(runs) == ["Mujica", "L-BFGS", "M02L03"]
+    cfg = OM.Config(**kw)
+    common = dict(checkpoint_every=every, nreal=nreal, fcounts=fcounts, box=box)
+    ref_m, ev_m, states = _oracle_run(s0, counts, R, cfg, it_m, True, 4, 1.0, **common)
+    ref_l, ev_l, _ = _oracle_run(s0, counts, R, cfg, it_m, False, 0, 0.1, **common)
+    ref_w, ev_w, _ = _oracle_run(states[2], counts, R, cfg, 3 * every, False, 0, 1.0, **common)
+    for name, ref, ev in (("Mujica", ref_m, ev_m), ("L-BFGS", ref_l, ev_l), ("M02L03", ref_w, ev_w)):
+        got = runs[name]
+        assert got["failed"] is None, name
+        assert [c[0] for c in got["curve"]] == [c[0] for c in ref], name
+        for (_, la, fa), (_, lb_, fb) in zip(got["curve"], ref):
+            assert abs(la - lb_) <= 1e-7 * abs(lb_), (name, la, lb_)
+            assert abs(fa - fb) <= 1e-7 * abs(fb), (name, fa, fb)
+        assert got["evals"] == ev, (name, got["evals"], ev)

@@ -8,7 +8,7 @@ import pytest
 from oracle import cosmology as C
 from oracle import mesh as M
 from oracle import model
-from oracle import power
+from oracle import analysis
 from paper_2604_26823_gb300 import inputs
 
 
@@ -38,9 +38,16 @@ def test_linear_field_power_spectrum_matches_input(table):
     cfg = model.Config(n=n, box=box)
     s = inputs.white_noise(n, 12).astype(np.float64)
     dl = model.linear_field(s, cfg, lnk, lnp)
-    edges = np.linspace(2 * np.pi / box, np.pi * n / box, 12)
-    k, pk, nm = power.power_spectrum(dl, box, edges)
-    ptab = C.power_from_table(k, lnk, lnp)
+    nb, kmin, kmax = 11, 2 * np.pi / box, np.pi * n / box
+    pk, _, _, nm = analysis.power_spectra(dl, None, box, nb, kmin, kmax)
+    # expectation of the estimator: the table averaged over each bin's modes
+    m = np.fft.fftfreq(n, 1.0 / n)
+    kk = 2 * np.pi / box * np.sqrt(m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2).ravel()
+    idx = np.floor((kk - kmin) / ((kmax - kmin) / nb)).astype(np.int64)
+    ok = (idx >= 0) & (idx < nb)
+    ptab = np.bincount(idx[ok], C.power_from_table(kk[ok], lnk, lnp), nb) / np.bincount(idx[ok], minlength=nb)
+    # each independent mode appears twice among the n^3 (its conjugate), so the
+    # relative scatter of a bin is sqrt(2 / N_modes)
     z = (pk / ptab - 1) / np.sqrt(2.0 / nm)
     assert np.all(np.abs(z) < 5.0)
     assert abs(np.mean(pk[2:] / ptab[2:]) - 1) < 0.05

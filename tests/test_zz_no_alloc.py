@@ -29,6 +29,15 @@ def test_noalloc_projection_matches_plan_projection_twice(prec):
         nb = api.pm_project_noalloc(b, seed=6, counter=counter)
         assert na == nb == (3 if call == 0 else 0)
         np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=tol, atol=tol)
+    # NaN input or zero variance: an error, and the vector keeps its values
+    bad = b.clone()
+    bad.view(-1)[5] = float("nan")
+    for vec in (bad, torch.full_like(b, 2.5)):
+        before = vec.cpu().numpy().copy()
+        with pytest.raises(api.L.PMError) as err:
+            api.pm_project_noalloc(vec, seed=6, counter=13)
+        assert err.value.status == api.L.PM_ERR_NONFINITE
+        np.testing.assert_array_equal(vec.cpu().numpy(), before)
     # sizes beyond the static scratch are refused with a clear error
     lib = api.L.load()
     st = lib.pm_project_noalloc(2 ** 28 + 1, 0, api.ctypes.c_void_p(b.data_ptr()), 0, 0, None, None)
