@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <string>
 
@@ -44,12 +45,10 @@ __device__ __forceinline__ void fx_add(unsigned long long *p, long long q) {
   atomicAdd(p, (unsigned long long)q);
 }
 
-// FP32 <-> int64 conversions written with integer operations from the
-// IEEE-754 binary32 layout (round to nearest, ties to even).  The hardware
-// conversions between FP32 and 64-bit integers issue on the FP64 unit,
-// which is narrow on this GPU and limited the fixed-point paint; these use
-// the integer and bit-manipulation units instead.  Both are host-callable
-// so they can be checked exhaustively on the CPU.
+// FP32 <-> int64 conversions (round to nearest, ties to even) that avoid the
+// hardware conversions between FP32 and 64-bit integers, which issue on the
+// FP64 unit -- narrow on this GPU, it limited the fixed-point paint.  Both are
+// host-callable so they can be checked exhaustively on the CPU.
 __host__ __device__ __forceinline__ unsigned fx_f32_bits(float w) {
 #ifdef __CUDA_ARCH__
   return __float_as_uint(w);
@@ -76,24 +75,23 @@ __host__ __device__ __forceinline__ int fx_clz64(unsigned long long v) {
 #endif
 }
 
-// rint(w) as int64 for |w| < 2^62 (larger magnitudes saturate the shift).
-__host__ __device__ __forceinline__ long long fx_f32_to_i64(float w) {
+// rint(w) as int64 for |w| < 2^61 with one FP32 -> int32 conversion: below
+// 2^31 the conversion itself is exact; above, w is an integer (its 24
+// significant bits sit at 2^(e-23) and higher), so w 2^-s with
+// s = exponent - 30 is still an integer below 2^31, converted exactly, and
+// shifted back.  The FP32 -> int32 conversion issues on the FP32 side of the
+// SM, not on the narrow FP64 unit that the FP32 -> int64 conversion uses.
+__host__ __device__ __forceinline__ long long fx_f32_to_i64_split(float w) {
   const unsigned b = fx_f32_bits(w);
   const int be = (int)((b >> 23) & 0xffu);
-  if (be < 126) return 0;  // |w| < 0.5, zero and subnormals
-  const unsigned m = (b & 0x7fffffu) | 0x800000u;  // |w| = m * 2^(be - 150)
-  const int sh = be - 150;
-  unsigned long long mag;
-  if (sh >= 0) {
-    mag = (unsigned long long)m << (sh < 39 ? sh : 39);
-  } else {
-    const int r = -sh;  // 1 .. 24
-    unsigned q = m >> r;
-    const unsigned rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
-    q += (rem > half || (rem == half && (q & 1u))) ? 1u : 0u;
-    mag = q;
-  }
-  return (b >> 31) ? -(long long)mag : (long long)mag;
+  const int s = be > 157 ? be - 157 : 0;                 // |w| < 2^(be - 126)
+  const float y = w * fx_bits_f32((unsigned)(127 - s) << 23);  // exact power-of-two scale
+#ifdef __CUDA_ARCH__
+  const int i = __float2int_rn(y);
+#else
+  const int i = (int)std::nearbyint(y);
+#endif
+  return (long long)((unsigned long long)(long long)i << s);
 }
 
 // Nearest float to the int64 q.

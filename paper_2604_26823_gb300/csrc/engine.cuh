@@ -145,7 +145,7 @@ inline bool lightcone_states(const pm_config &c, int (&ks)[2]) {
 
 struct Layout {
   size_t tw, amp, spec, fx, psi, psi2, src, dbar, mom, xbar, pbar, disp, phi, ckd, ckm, dwork, snap, lct, scal,
-      perm, tslot, tcnt, total;
+      total;
   int nck, seglen;
 };
 
@@ -195,18 +195,6 @@ inline Layout make_layout(const pm_config &c) {
     L.lct = take(3 * kLcTable * es);        // a_j, chi_j, slope_j
   }
   L.scal = take(64 * 1024);
-  // tile binning of the particles (tile-binned deposition): the particle
-  // order by tile, each particle's (tile, slot), the per-tile counts and
-  // offsets
-  // (one particle order and one offset table per stored state, like the
-  // state history)
-  int logn = 0;
-  while ((1 << logn) < c.n) ++logn;
-  const part::TileGeo tg = part::tile_geo(logn);
-  const size_t nps = (size_t)L.seglen;
-  L.perm = take(nps * m * 4);
-  L.tslot = take(m * 8);
-  L.tcnt = take(((size_t)tg.ntiles + nps * ((size_t)tg.ntiles + 1)) * 4);
   L.total = off;
   return L;
 }
@@ -241,9 +229,6 @@ template <typename T> struct Engine {
   int *fx_exp = nullptr;
   unsigned long long *maxslot = nullptr;
   unsigned long long *maxslots = nullptr;  // part::kMaxSlots partial maxima (zero between uses)
-  part::TileGeo tg{};
-  unsigned *perm = nullptr, *tcount = nullptr, *toff = nullptr;
-  unsigned long long *tslot = nullptr;
   void *sort_ws = nullptr;
   Profiler prof;
 
@@ -312,11 +297,6 @@ template <typename T> struct Engine {
         return PM_ERR_UNSUPPORTED;
       }
     }
-    tg = part::tile_geo(logn);
-    perm = reinterpret_cast<unsigned *>(base + lay.perm);
-    tslot = reinterpret_cast<unsigned long long *>(base + lay.tslot);
-    tcount = reinterpret_cast<unsigned *>(base + lay.tcnt);
-    toff = tcount + tg.ntiles;
     char *sc = base + lay.scal;
     partial = reinterpret_cast<double *>(sc);
     results = partial + pw::kRedBlocks;
@@ -538,54 +518,6 @@ template <typename T> struct Engine {
     return PM_OK;
   }
 
-  // Tile order of the particles of a stored state (the same slots as the
-  // state history): perm_of lists each tile's particles, toff_of the tiles'
-  // offsets.
-  unsigned *perm_of(int slot) const { return perm + (int64_t)slot * M; }
-  unsigned *toff_of(int slot) const { return toff + (int64_t)slot * (tg.ntiles + 1); }
-  // offsets and order of a slot from the counts and (tile, slot) words of a binning pass
-  pm_status finish_bin(int slot) {
-    ::pm::note_launch();
-    part::k_bin_scan<<<1, 1024, 0, st>>>(tcount, tg.ntiles, toff_of(slot));
-    ::pm::note_launch();
-    part::k_bin_scatter<<<grid_for(M, 256), 256, 0, st>>>(M, tslot, toff_of(slot), perm_of(slot));
-    PM_LAUNCH_CHECK();
-    return PM_OK;
-  }
-  // Tile binning of the particles at positions x (cell units) into a slot.
-  pm_status bin(const T *x, int slot) {
-    PM_CUDA_TRY(cudaMemsetAsync(tcount, 0, (size_t)tg.ntiles * sizeof(unsigned), st));
-    ::pm::note_launch();
-    part::k_bin_count<T><<<grid_for(M, 256), 256, 0, st>>>(geo(), tg, x, tcount, tslot);
-    PM_LAUNCH_CHECK();
-    return finish_bin(slot);
-  }
-  // One tile-binned deposition launch over the particles in the tile order
-  // of `slot`, into a shared box with a margin of MG cells; with
-  // bin_slot >= 0 the particles are binned at their deposit positions into
-  // that slot (which may be `slot` itself: the order is rewritten after the
-  // launch).
-  template <int MG, class Src> pm_status deposit_tiled(Src s, int slot, int bin_slot = -1) {
-    const size_t sm = part::tile_box_bytes(tg, Src::NCH, MG);
-    unsigned long long *mesh = reinterpret_cast<unsigned long long *>(fx);
-    if (bin_slot >= 0) {
-      PM_CUDA_TRY(cudaMemsetAsync(tcount, 0, (size_t)tg.ntiles * sizeof(unsigned), st));
-      auto kern = part::k_deposit_tiled<T, Src, MG, true>;
-      set_smem(kern, sm);
-      ::pm::note_launch();
-      kern<<<tg.ntiles, 256, sm, st>>>(geo(), tg, s, perm_of(slot), toff_of(slot), mesh, M,
-                                        part::BinOut{tcount, tslot});
-      PM_LAUNCH_CHECK();
-      return finish_bin(bin_slot);
-    }
-    auto kern = part::k_deposit_tiled<T, Src, MG, false>;
-    set_smem(kern, sm);
-    ::pm::note_launch();
-    kern<<<tg.ntiles, 256, sm, st>>>(geo(), tg, s, perm_of(slot), toff_of(slot), mesh, M, part::BinOut{});
-    PM_LAUNCH_CHECK();
-    return PM_OK;
-  }
-
   // ---- forward stages ----
   // 2LPT: fills disp0 / mom (cell units), phi_ij (when keep), paints density.
   pm_status lpt(const T *s, T *disp0, bool paint) {
@@ -628,15 +560,14 @@ template <typename T> struct Engine {
     }
     const double ic = 1.0 / cell;
     const part::Geo g = geo();
-    PM_TRY(deposit(part::SrcLpt<T>{g.L, M, psi, cfg.lpt_order == 2 ? psi2 : nullptr, (T)(d1 * ic), (T)(d2 * ic),
-                                   (T)(gp1 * ic), (T)(gp2 * ic), disp0, mom, paint ? fx_exp : nullptr, T(0)}));
-    // tile order of the initial state (slot 0) for the first leapfrog step
-    return bin(disp0, 0);
+    return deposit(part::SrcLpt<T>{g.L, M, psi, cfg.lpt_order == 2 ? psi2 : nullptr, (T)(d1 * ic), (T)(d2 * ic),
+                                   (T)(gp1 * ic), (T)(gp2 * ic), disp0, mom, paint ? fx_exp : nullptr, T(0)});
   }
 
-  // PM force mesh (cell units) from the painted density in fx channel 0
-  // (transformed as delta = rho - 1, N_mesh = N_part).
-  pm_status force_mesh(V4<T> *out) {
+  // PM force mesh (cell units) of stored state `si` from the painted density
+  // in fx channel 0 (transformed as delta = rho - 1, N_mesh = N_part).
+  pm_status force_mesh(int si) {
+    V4<T> *out = pstate(si);
     PM_TRY(r2c_fixed(fx, fx_exp, 1, slot(0), true));
     PM_TRY(ypass(slot(0), 1, -1));
     fft::MultDesc m[3];
@@ -663,9 +594,8 @@ template <typename T> struct Engine {
       PM_TRY(memset_fx(1));
       {
         // method: x, p read and written, 3 force components read, density written;
-        // implementation: float4 force mesh, 64-bit fixed-point density, the
-        // particle order read and the next state's binning words written
-        ProfScope ps(prof, P_KDK, st, (double)M * 16 * sizeof(T), (double)M * (16 * sizeof(T) + 8 + 4 + 8));
+        // implementation: float4 force mesh, 64-bit fixed-point density
+        ProfScope ps(prof, P_KDK, st, (double)M * 16 * sizeof(T), (double)M * (16 * sizeof(T) + 8));
         part::SrcKdk<T> src_k{g.L, M, pstate(si), dstate(si), dstate(so), momb, (T)ck[k], (T)dr[k], fx_exp, T(0)};
         if (lc_on && lc_write && (k == lc_k[0] || k == lc_k[1])) {
           const int j = k == lc_k[0] ? 0 : 1;
@@ -673,12 +603,9 @@ template <typename T> struct Engine {
           src_k.snap_p = snap + (int64_t)(2 + j) * 3 * M;
           src_k.kb = (T)kbv[k];
         }
-        // particles in the tile order of x_k; x_{k+1} deposited (a particle
-        // that moved more than 2 cells out of its tile goes to the mesh
-        // directly) and binned into the order of the next state
-        PM_TRY((deposit_tiled<2>(src_k, si, so)));
+        PM_TRY(deposit(src_k));
       }
-      PM_TRY(force_mesh(pstate(so)));
+      PM_TRY(force_mesh(so));
     }
     return PM_OK;
   }
@@ -688,7 +615,7 @@ template <typename T> struct Engine {
   pm_status forward_to_density(const T *s, bool keep) {
     const int ns = cfg.n_steps;
     PM_TRY(lpt(s, dstate(0), true));
-    PM_TRY(force_mesh(pstate(0)));
+    PM_TRY(force_mesh(0));
     if (keep_all() || !keep) {
       PM_TRY(run_steps(0, ns, 0, keep && keep_all(), mom));
     } else {
@@ -719,9 +646,7 @@ template <typename T> struct Engine {
       fsrc.lightcone = true;
       fsrc.lc = lightcone();
     }
-    // in the tile order of the final state (a redshift-space or lightcone
-    // shift of more than 2 cells goes to the mesh directly)
-    return deposit_tiled<2>(fsrc, fin);
+    return deposit(fsrc);
   }
 
   pm_status loss_terms(const T *s, const T *data, const T *R, const T *cot, double lw, bool want_dbar,
@@ -809,12 +734,10 @@ template <typename T> struct Engine {
     PM_TRY(memset_fx(3));
     {
       // method (the 3-channel paint's 24 B / particle in FP32): positions read,
-      // three mesh channels written; implementation: positions, cotangent and
-      // the particle order read, 64-bit fixed-point channels
-      ProfScope ps(prof, P_ADJ_PAINT, st, (double)M * 6 * sizeof(T), (double)M * (6 * sizeof(T) + 4 + 24));
-      // in the tile order of state k (binned when the state was made)
-      PM_TRY((deposit_tiled<0>(part::SrcAdj3<T>{g.L, M, g.log2np, xk, pbar, (T)ck[k], maxslot, fx_exp + 1, 0},
-                               slot)));
+      // three mesh channels written; implementation: positions and cotangent
+      // read, 64-bit fixed-point channels
+      ProfScope ps(prof, P_ADJ_PAINT, st, (double)M * 6 * sizeof(T), (double)M * (6 * sizeof(T) + 24));
+      PM_TRY(deposit(part::SrcAdj3<T>{g.L, M, g.log2np, xk, pbar, (T)ck[k], maxslot, fx_exp + 1, 0}));
     }
     PM_TRY(adjoint_force(src));
     const T drift = k > 0 ? (T)dr[k - 1] : T(0);
@@ -891,8 +814,7 @@ template <typename T> struct Engine {
         PM_TRY(memset_fx(1));
         PM_TRY(set_exp(0, rho_exp));
         PM_TRY(deposit(part::SrcPaint<T>{g.L, M, dstate(0), psi2, -1, T(0), fx_exp, T(0)}));
-        PM_TRY(bin(dstate(0), 0));
-        PM_TRY(force_mesh(pstate(0)));
+        PM_TRY(force_mesh(0));
         lc_write = false;  // the snapshot buffer holds their cotangents now
         const pm_status rs = run_steps(lo, hi, lo, true, psi2);
         lc_write = true;
@@ -1091,7 +1013,7 @@ template <typename T> struct Engine {
       pw::k_fixed_to_delta<T><<<grid_for(M, 256), 256, 0, st>>>(fx, fx_exp, density_out, M);
       PM_LAUNCH_CHECK();
     }
-    PM_TRY(force_mesh(pstate(0)));
+    PM_TRY(force_mesh(0));
     ::pm::note_launch();
     part::k_readout<T><<<grid_for(M, 256), 256, 0, st>>>(geo(), pstate(0), dstate(0), (T)cell, force_out);
     PM_LAUNCH_CHECK();
@@ -1099,7 +1021,7 @@ template <typename T> struct Engine {
   }
   pm_status probe_evolve(const T *s, T *disp_out, T *mom_out) {
     PM_TRY(lpt(s, dstate(0), true));
-    PM_TRY(force_mesh(pstate(0)));
+    PM_TRY(force_mesh(0));
     PM_TRY(run_steps(0, cfg.n_steps, 0, false, mom));
     PM_TRY(deposit(part::SrcFinal<T>{geo().L, M, pstate(0), dstate(0), mom, (T)ck[cfg.n_steps], -1, T(0),
                                          nullptr, T(0)}));

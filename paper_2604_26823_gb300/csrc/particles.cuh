@@ -58,17 +58,12 @@ template <typename T> __device__ __forceinline__ T pow2(int e) {
   else return ldexp(1.0, e);
 }
 
-// A deposit rint(w) of a weight already scaled by 2^E, as an integer.  For
-// FP32 the two exact round-to-nearest conversions run on different units
-// (HW: the hardware conversion, on the FP64 unit; otherwise integer
-// operations): the deposit kernel alternates them so neither unit limits it.
-template <typename T, bool HW> __device__ __forceinline__ long long fx_round(T w) {
-  if constexpr (sizeof(T) == 4) {
-    if constexpr (HW) return __float2ll_rn(w);
-    else return fx_f32_to_i64(w);
-  } else {
-    return __double2ll_rn(w);
-  }
+// A deposit rint(w) of a weight already scaled by 2^E, as an integer: FP32
+// through one FP32 -> int32 conversion and a shift (exact, fx_f32_to_i64_split),
+// FP64 through the hardware conversion.
+template <typename T> __device__ __forceinline__ long long fx_round(T w) {
+  if constexpr (sizeof(T) == 4) return fx_f32_to_i64_split(w);
+  else return __double2ll_rn(w);
 }
 
 // F = sum_c W(u - c) Phi(c) over a 4-component mesh (x, y, z used).
@@ -479,6 +474,7 @@ template <typename T> struct SrcFinal {
 
 // 3-channel force cotangent c_k * pbar at x_k, fixed point with the exponent
 // chosen from the running max of |c_k pbar| (written to fx_exp_out).
+
 template <typename T> struct SrcAdj3 {
   static constexpr int NCH = 3;
   Lattice L;
@@ -521,6 +517,7 @@ template <typename T> struct SrcAdj3 {
 // down by a shuffle and added here, so that lane issues only its upper-z
 // atomics.  The merged sums are sums of the same integers, so the mesh is
 // unchanged bit for bit, with up to half the atomics.
+
 template <typename T, class Src>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_deposit(Geo g, Src src, unsigned long long *mesh, int64_t plane) {
   constexpr int NCH = Src::NCH;
@@ -550,8 +547,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_deposit(Geo g, 
 #pragma unroll
       for (int oy = 0; oy < 2; ++oy) {
         const T wxy = wx[ox] * wy[oy] * v[ch];
-        long long q0 = live ? fx_round<T, true>(wxy * wz[0]) : 0;
-        long long q1 = live ? fx_round<T, false>(wxy * wz[1]) : 0;
+        long long q0 = live ? fx_round<T>(wxy * wz[0]) : 0;
+        long long q1 = live ? fx_round<T>(wxy * wz[1]) : 0;
         const long long up0 = __shfl_down_sync(kFull, q0, 1);
         if (merge_up) q1 += up0;
         if (live) {
@@ -560,210 +557,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_deposit(Geo g, 
           if (q1) fx_add(col + z1, q1);
         }
       }
-  }
-}
-
-// ---- tile-binned deposition ------------------------------------------------
-// The mesh is cut into Eulerian tiles of TX x TY x TZ cells (8 x 8 x 32, each
-// side capped at n).  A counting sort by the tile of each particle's base
-// cell (k_bin_count -> k_bin_scan -> k_bin_scatter) lists every tile's
-// particles; k_deposit_tiled then runs one CTA per tile, accumulates the
-// tile's CIC deposits in shared memory and adds the box to the mesh with one
-// coalesced 64-bit integer reduction per non-zero node.  A particle's 8 nodes
-// lie in the box [tile origin - MG, tile end + MG] when its base cell lies in
-// the tile extended by MG cells; nodes outside the box (a particle that moved
-// since it was binned) go straight to the mesh with global integer atomics,
-// so any particle order gives the same mesh.
-//
-// The shared accumulators hold the same 64-bit fixed-point sums as the mesh,
-// as two 32-bit words per node: the low word is added with an atomic that
-// returns its old value, its carry out is detected from that value, and the
-// high word receives the high half plus the carry.  That is exact 64-bit
-// two's-complement addition, so the sums -- and the painted mesh -- do not
-// depend on the order of the deposits (deterministic deposition), and the
-// binning may use atomics to place particles within a tile.
-struct TileGeo {
-  int ltx, lty, ltz;  // log2 of the tile extent along x, y, z (cells)
-  int lny, lnz;       // log2 of the number of tiles along y and z
-  int ntiles;
-  __host__ __device__ int tile_of(int cx, int cy, int cz) const {
-    return ((cx >> ltx) << (lny + lnz)) | ((cy >> lty) << lnz) | (cz >> ltz);
-  }
-};
-
-// Tile geometry of an n^3 mesh (logn = log2 n).
-inline TileGeo tile_geo(int logn) {
-  TileGeo t;
-  t.ltx = logn < 3 ? logn : 3;
-  t.lty = t.ltx;
-  t.ltz = logn < 5 ? logn : 5;
-  t.lny = logn - t.lty;
-  t.lnz = logn - t.ltz;
-  t.ntiles = 1 << (3 * logn - t.ltx - t.lty - t.ltz);
-  return t;
-}
-
-// Shared-memory bytes of the deposit box of NCH channels with margin mg.
-inline size_t tile_box_bytes(const TileGeo &t, int nch, int mg) {
-  const size_t bx = (1 << t.ltx) + 1 + 2 * mg, by = (1 << t.lty) + 1 + 2 * mg, bz = (1 << t.ltz) + 1 + 2 * mg;
-  return bx * by * bz * (size_t)nch * 8;
-}
-
-// Per particle: the tile of its base cell at positions x, and its slot within
-// the tile (warp-aggregated atomic on the tile's counter); packed as
-// (tile << 32) | slot.  count[] must be zero before the launch.
-template <typename T>
-__global__ void k_bin_count(Geo g, TileGeo tg, const T *__restrict__ x, unsigned *count,
-                            unsigned long long *tslot) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  unsigned t = 0x80000000u | (unsigned)lane;  // matches no real tile
-  if (p < g.np) {
-    const Cell<T> c = locate<T>(g.L, p, x[p], x[g.np + p], x[2 * g.np + p]);
-    t = (unsigned)tg.tile_of(c.c[0], c.c[1], c.c[2]);
-  }
-  const unsigned peers = __match_any_sync(0xffffffffu, t);
-  const int leader = __ffs(peers) - 1;
-  const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-  unsigned base = 0;
-  if (p < g.np && lane == leader) base = atomicAdd(count + t, (unsigned)__popc(peers));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (p < g.np) tslot[p] = ((unsigned long long)t << 32) | (base + rank);
-}
-
-// off[0..ntiles] = exclusive prefix sums of count[0..ntiles) (one block).
-static __global__ void __launch_bounds__(1024) k_bin_scan(const unsigned *__restrict__ count, int ntiles,
-                                                          unsigned *off) {
-  __shared__ unsigned sh[1024];
-  unsigned carry = 0;
-  for (int base = 0; base < ntiles; base += 1024) {
-    const int i = base + threadIdx.x;
-    const unsigned v = i < ntiles ? count[i] : 0u;
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const unsigned a = threadIdx.x >= o ? sh[threadIdx.x - o] : 0u;
-      __syncthreads();
-      sh[threadIdx.x] += a;
-      __syncthreads();
-    }
-    if (i < ntiles) off[i] = carry + sh[threadIdx.x] - v;
-    carry += sh[1023];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) off[ntiles] = carry;
-}
-
-// perm[off[tile] + slot] = p.
-static __global__ void k_bin_scatter(int64_t np, const unsigned long long *__restrict__ tslot,
-                                     const unsigned *__restrict__ off, unsigned *perm) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  const unsigned long long ts = tslot[p];
-  perm[off[ts >> 32] + (unsigned)ts] = (unsigned)p;
-}
-
-// Exact 64-bit add of q into the (lo, hi) word pair of one shared node.
-__device__ __forceinline__ void sh_add64(unsigned *lo, unsigned *hi, long long q) {
-  const unsigned ql = (unsigned)(unsigned long long)q;
-  const unsigned qh = (unsigned)((unsigned long long)q >> 32);
-  const unsigned old = atomicAdd(lo, ql);
-  const unsigned carry = (old + ql) < old ? 1u : 0u;
-  const unsigned h = qh + carry;
-  if (h) atomicAdd(hi, h);
-}
-
-// Where a deposition launch also bins the particles at their deposit
-// positions (k_bin_count's output, for the next launch's order): count must
-// be zero before the launch; null: no binning.
-struct BinOut {
-  unsigned *count = nullptr;
-  unsigned long long *tslot = nullptr;
-};
-
-// One CTA per tile: deposits of the tile's particles (perm[off[t] ..
-// off[t + 1])), through the source functor, into the shared box of margin MG,
-// then the box added to the mesh.  With BIN, each particle's deposit cell is
-// also binned into bo (as k_bin_count).  Shared memory:
-// tile_box_bytes(tg, NCH, MG).
-template <typename T, class Src, int MG, bool BIN>
-__global__ void __launch_bounds__(256) k_deposit_tiled(Geo g, TileGeo tg, Src src, const unsigned *__restrict__ perm,
-                                                      const unsigned *__restrict__ off, unsigned long long *mesh,
-                                                      int64_t plane, BinOut bo) {
-  constexpr int NCH = Src::NCH;
-  extern __shared__ unsigned shbox[];
-  const int t = blockIdx.x;
-  const int mask = g.L.mask, logn = g.L.logn;
-  const int bx = (1 << tg.ltx) + 1 + 2 * MG, by = (1 << tg.lty) + 1 + 2 * MG, bz = (1 << tg.ltz) + 1 + 2 * MG;
-  const int nb = bx * by * bz;
-  const int ox = ((t >> (tg.lny + tg.lnz)) << tg.ltx) - MG;
-  const int oy = (((t >> tg.lnz) & ((1 << tg.lny) - 1)) << tg.lty) - MG;
-  const int oz = ((t & ((1 << tg.lnz) - 1)) << tg.ltz) - MG;
-  unsigned *lo = shbox, *hi = shbox + NCH * nb;
-  for (int i = threadIdx.x; i < 2 * NCH * nb; i += blockDim.x) shbox[i] = 0u;
-  Src s = src;
-  s.setup();
-  __syncthreads();
-  const unsigned beg = off[t], end = off[t + 1];
-  const int lane = threadIdx.x & 31;
-  // the trip count is the same for every thread of the block, so the warp
-  // is converged at the binning's match below
-  for (unsigned base = beg; base < end; base += blockDim.x) {
-    const unsigned i = base + threadIdx.x;
-    const bool valid = i < end;
-    const int64_t p = valid ? perm[i] : 0;
-    Cell<T> c{};
-    T v[NCH];
-    const bool live = valid && s(p, c, v);
-    if constexpr (BIN) {
-      const unsigned tb = valid ? (unsigned)tg.tile_of(c.c[0], c.c[1], c.c[2]) : (0x80000000u | (unsigned)lane);
-      const unsigned peers = __match_any_sync(0xffffffffu, tb);
-      const int leader = __ffs(peers) - 1;
-      const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-      unsigned b0 = 0;
-      if (valid && lane == leader) b0 = atomicAdd(bo.count + tb, (unsigned)__popc(peers));
-      b0 = __shfl_sync(0xffffffffu, b0, leader);
-      if (valid) bo.tslot[p] = ((unsigned long long)tb << 32) | (b0 + rank);
-    }
-    if (!live) continue;
-    const T wx[2] = {T(1) - c.f[0], c.f[0]};
-    const T wy[2] = {T(1) - c.f[1], c.f[1]};
-    const T wz[2] = {T(1) - c.f[2], c.f[2]};
-#pragma unroll
-    for (int cx = 0; cx < 2; ++cx) {
-      const int gx = (c.c[0] + cx) & mask, lx = (gx - ox) & mask;
-#pragma unroll
-      for (int cy = 0; cy < 2; ++cy) {
-        const int gy = (c.c[1] + cy) & mask, ly = (gy - oy) & mask;
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-          // the same weight products and conversions as k_deposit
-          const T wxy = wx[cx] * wy[cy] * v[ch];
-#pragma unroll
-          for (int cz = 0; cz < 2; ++cz) {
-            const long long q = cz ? fx_round<T, false>(wxy * wz[1]) : fx_round<T, true>(wxy * wz[0]);
-            if (!q) continue;
-            const int gz = (c.c[2] + cz) & mask, lz = (gz - oz) & mask;
-            if (lx < bx && ly < by && lz < bz) {
-              const int li = ch * nb + (lx * by + ly) * bz + lz;
-              sh_add64(lo + li, hi + li, q);
-            } else {
-              fx_add(mesh + ch * plane + (((((int64_t)gx << logn) | gy) << logn) | gz), q);
-            }
-          }
-        }
-      }
-    }
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    const int lz = j % bz, r = j / bz, ly = r % by, lx = r / by;
-    const int64_t gi = (((((int64_t)((ox + lx) & mask)) << logn) | ((oy + ly) & mask)) << logn) | ((oz + lz) & mask);
-#pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) {
-      const unsigned long long q = ((unsigned long long)hi[ch * nb + j] << 32) | lo[ch * nb + j];
-      if (q) atomicAdd(mesh + ch * plane + gi, q);
-    }
   }
 }
 

@@ -150,10 +150,17 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
   const int e = -__ldg(fx_exp);
   SumAcc<T> acc;  // the likelihood terms, each formed in T
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T delta;
-    // delta = rho - 1 formed in integers (one unit weight is 2^-e), then rounded once
-    if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
-    else delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
+    // delta = rho - 1 formed in integers (one unit weight is 2^-e) and
+    // 1 + delta = rho, each rounded once from the exact fixed-point value, so
+    // both keep full relative precision (delta near 0, rho near the floor)
+    T delta, onep;
+    if constexpr (sizeof(T) == 4) {
+      delta = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
+      onep = scalbnf(fx_i64_to_f32(rho[i]), e);
+    } else {
+      delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
+      onep = scalbn(__ll2double_rn(rho[i]), e);
+    }
     if (delta_out) delta_out[i] = delta;
     const T r = resp[i];
     T g = T(0);
@@ -162,7 +169,6 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
       acc.add(T(0.5) * r * res * res * (T)lp.inv_s2);
       g = r * (T)lp.b * res * (T)lp.inv_s2;
     } else if (r > T(0)) {
-      const T onep = T(1) + delta;
       const T base = onep > (T)lp.rho_floor ? onep : (T)lp.rho_floor;
       const T sg = T(1) / (T(1) + exp(-(T)lp.K * (delta - (T)lp.delta_th)));
       const T pw = pow(base, (T)lp.alpha);
@@ -185,13 +191,17 @@ __global__ void k_expected(LossParams lp, const long long *__restrict__ rho, con
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int e = -__ldg(fx_exp);
-  T delta;
-  if constexpr (sizeof(T) == 4) delta = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
-  else delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
+  T delta, onep;
+  if constexpr (sizeof(T) == 4) {
+    delta = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
+    onep = scalbnf(fx_i64_to_f32(rho[i]), e);
+  } else {
+    delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
+    onep = scalbn(__ll2double_rn(rho[i]), e);
+  }
   if (lp.lik == 0) {
     out[i] = (T)lp.b * delta;
   } else {
-    const T onep = T(1) + delta;
     const T base = onep > (T)lp.rho_floor ? onep : (T)lp.rho_floor;
     const T sg = T(1) / (T(1) + exp(-(T)lp.K * (delta - (T)lp.delta_th)));
     out[i] = resp[i] > T(0) ? resp[i] * (T)lp.nbar * pow(base, (T)lp.alpha) * sg : T(0);

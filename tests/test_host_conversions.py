@@ -1,7 +1,8 @@
-"""The integer-pipe FP32 <-> int64 conversions of the deposits and of the
-fixed-point loader (csrc/common.cuh) equal round-to-nearest-even conversions
-on ~4.4e7 floats and ~2e7 integers (halfway cases and extremes included).
-Host code compiled with nvcc; no GPU needed."""
+"""The FP32 <-> int64 conversions of the deposits (one FP32 -> int32
+conversion and a shift) and of the fixed-point loader (integer pipe),
+csrc/common.cuh, equal round-to-nearest-even conversions on ~4.4e7 floats
+and ~2e7 integers (halfway cases, the split's boundaries and extremes
+included).  Host code compiled with nvcc; no GPU needed."""
 import os
 import shutil
 import subprocess
