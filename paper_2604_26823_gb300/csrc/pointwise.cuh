@@ -275,9 +275,13 @@ template <typename T> __global__ void k_fma_probe(int64_t iters, T *__restrict__
   const T m = T(0.999999), c = T(1e-7);
 #pragma unroll
   for (int j = 0; j < 8; ++j) a[j] = T(threadIdx.x + j) * T(1e-3);
-  for (int64_t i = 0; i < iters; ++i) {
+  const int it = (int)iters;
+  for (int i = 0; i < it; ++i) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+    for (int j = 0; j < 8; ++j) {
+      if constexpr (sizeof(T) == 4) a[j] = fmaf(a[j], m, c);  // the FP32 instruction, no promotion
+      else a[j] = fma(a[j], m, c);
+    }
   }
   T s = T(0);
 #pragma unroll

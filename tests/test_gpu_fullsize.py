@@ -3,7 +3,7 @@ likelihood, the launch configuration bench.py times), checked through
 properties that hold at any size -- the FP64 oracle cannot evaluate a 256^3
 gradient in test time:
   * FP32 path vs the all-FP64 GPU path: loss and density within 1e-5, the
-    gradient's cosine >= 0.99999;
+    gradient's cosine >= 0.99999 and relative L2 < 4.7e-4 (1.5 x measured);
   * the FP64 path's gradient against its own central differences along
     seeded random directions (eps = 1e-3);
   * bit-identical repeated evaluation, and bit-identical gradients with
@@ -55,7 +55,9 @@ def test_fp32_vs_fp64_at_full_size(setup):
     print(f"256^3 FP32 vs FP64 path: loss {abs(l32 - l64) / abs(l64):.2e}, density "
           f"{np.linalg.norm(d32 - d64) / np.linalg.norm(d64):.2e}, gradient rel L2 {err:.3e} cos {cos:.9f}")
     assert cos > 0.99999
-    assert err < 2e-3
+    # measured 3.10e-4 .. 3.17e-4 on a GB300 (the CIC face crossings of the
+    # FP32 trajectory, as in test_gpu_model's FP32 bound); 1.5 x that
+    assert err < 4.7e-4
 
 
 def test_fp64_gradient_against_finite_differences(setup):
@@ -73,7 +75,7 @@ def test_fp64_gradient_against_finite_differences(setup):
         errs.append(abs(fd - gu) / (abs(gu) + 1e-3 * float(g.norm())))
     del plan64
     print("256^3 FP64 gradient vs FD along 4 directions:", ["%.2e" % e for e in errs])
-    assert max(errs) < 1e-3, errs
+    assert max(errs) < 5e-4, errs   # measured 1.9e-4 at worst (eps = 1e-3 crosses cell faces)
 
 
 def test_repeatable_and_checkpoint_identical(setup):

@@ -230,7 +230,9 @@ def test_fd_directions_fp64_gpu(api):
         gu = float((g * u).sum())
         errs.append(abs(fd - gu) / (abs(gu) + 1e-3 * float(g.norm())))
     print("FD along 16 directions, FP64 GPU path, 128^3 RSD: median %.2e max %.2e" % (np.median(errs), max(errs)))
-    assert np.median(errs) < 1e-4 and max(errs) < 1e-2, errs
+    # measured median 6.7e-5, max 1.75e-4: a central difference with eps = 1e-3
+    # moves some particles across cell faces, where the CIC derivative jumps
+    assert np.median(errs) < 1e-4 and max(errs) < 5e-4, errs
 
 
 def test_pmloss_autograd(api):
