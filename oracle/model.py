@@ -10,10 +10,13 @@ Forward model (Sec. 2.2.1 items 1-5, Sec. 2.2.2):
      kick-drift-kick PM steps with FastPM factors to a = 1 (item 2);
   3. plane-parallel redshift-space shift along one axis (item 3, Eq. RSD with
      the line of sight fixed to a box axis);
-  4. galaxy bias: linear delta_g = b delta_m, or the power law + sigmoid of
-     Eq. galaxy_bias (item 4);
+  4. galaxy bias f(delta) (item 4): linear, b delta for the Gaussian and the
+     rate 1 + b delta (floored) for the Poisson; or the power law + sigmoid
+     of Eq. galaxy_bias, nbar g(delta) for the Gaussian and the rate g(delta)
+     for the Poisson.  By default ("auto") the Gaussian takes the linear and
+     the Poisson the power-law bias, the pairs Sec. 2.2.2 describes;
   5. survey response lambda_obs = R lambda (item 5);
-  6. likelihood: Gaussian (1/2) sum R (b delta - d)^2 / sigma^2, or the
+  6. likelihood: Gaussian (1/2) sum R (f(delta) - d)^2 / sigma^2, or the
      Poisson log-likelihood of Sec. 2.2.2 without the constant log N!;
   plus the Gaussian prior (w/2) sum s^2 on the white noise.
 
@@ -40,7 +43,8 @@ class Config:
     rsd_axis: int = -1          # -1: none, 0..2: plane-parallel shift along that axis, 3: radial
     observer: tuple = (0.0, 0.0, 0.0)   # Mpc/h, box coordinates (radial shift, lightcone)
     lightcone: bool = False     # observe each particle on the observer's past light cone (Appendix A)
-    likelihood: str = "gaussian"   # "gaussian" (linear bias) | "poisson" (power law + sigmoid)
+    likelihood: str = "gaussian"   # "gaussian" | "poisson"
+    bias: str = "auto"             # "auto" (gaussian: linear, poisson: power law) | "linear" | "powerlaw_sigmoid"
     bias_b: float = 1.5
     sigma: float = 1.0
     alpha: float = 0.7
@@ -330,10 +334,20 @@ def final_density(disp_obs, cfg):
     return M.cic_paint(positions_cells(disp_obs, cfg), cfg.n) - 1.0
 
 
-def _poisson_rate(delta, cfg):
-    """lambda / (R nbar) = max(1+delta, rho_floor)^alpha sigmoid(K (delta - delta_th))
-    (Eq. galaxy_bias with the floor that keeps the power law finite) and its
-    derivative wrt delta (zero below the floor for the power-law factor)."""
+def bias_kind(cfg):
+    """The bias model a configuration uses ("auto" resolves by likelihood)."""
+    if cfg.bias == "auto":
+        return "linear" if cfg.likelihood == "gaussian" else "powerlaw_sigmoid"
+    if cfg.bias not in ("linear", "powerlaw_sigmoid"):
+        raise ValueError(cfg.bias)
+    return cfg.bias
+
+
+def _powerlaw_sigmoid(delta, cfg):
+    """g = max(1+delta, rho_floor)^alpha sigmoid(K (delta - delta_th))
+    (Eq. galaxy_bias without its normalisation, with the floor that keeps the
+    power law finite) and its derivative wrt delta (zero below the floor for
+    the power-law factor)."""
     base = np.maximum(1.0 + delta, cfg.rho_floor)
     sig = _sigmoid(cfg.K * (delta - cfg.delta_th))
     g = base ** cfg.alpha * sig
@@ -342,15 +356,32 @@ def _poisson_rate(delta, cfg):
     return g, dg
 
 
+def _linear_rate(delta, cfg):
+    """g = max(1 + b delta, rho_floor): the mean galaxy density of the linear
+    bias model per unit nbar, floored so that the Poisson rate stays positive
+    where b delta < -1; derivative b above the floor, zero below it."""
+    base = 1.0 + cfg.bias_b * delta
+    g = np.maximum(base, cfg.rho_floor)
+    dg = np.where(base > cfg.rho_floor, cfg.bias_b, 0.0)
+    return g, dg
+
+
 def likelihood_terms(delta, data, resp, cfg):
-    """(-log L, d(-log L)/d delta) for the configured likelihood (Sec. 2.2.2)."""
+    """(-log L, d(-log L)/d delta) for the configured likelihood (Sec. 2.2.2)
+    and bias model."""
+    kind = bias_kind(cfg)
     if cfg.likelihood == "gaussian":
-        r = cfg.bias_b * delta - data
+        if kind == "linear":
+            f, df = cfg.bias_b * delta, cfg.bias_b
+        else:
+            g, dg = _powerlaw_sigmoid(delta, cfg)
+            f, df = cfg.nbar_cell * g, cfg.nbar_cell * dg
+        r = f - data
         val = 0.5 * np.sum(resp * r * r) / cfg.sigma ** 2
-        grad = resp * cfg.bias_b * r / cfg.sigma ** 2
+        grad = resp * df * r / cfg.sigma ** 2
         return val, grad
     if cfg.likelihood == "poisson":
-        g, dg = _poisson_rate(delta, cfg)
+        g, dg = (_linear_rate if kind == "linear" else _powerlaw_sigmoid)(delta, cfg)
         mask = resp > 0
         lam = np.where(mask, resp * cfg.nbar_cell * g, 1.0)
         val = np.sum(np.where(mask, lam - data * np.log(lam), 0.0))

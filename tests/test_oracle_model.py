@@ -156,10 +156,13 @@ def _cases():
         # radial shift from an observer outside the box (the paper's line of sight)
         model.Config(n=8, box=32.0, n_steps=2, lpt_order=2, rsd_axis=3, observer=(16.0, 20.0, -24.0),
                      likelihood="gaussian", bias_b=1.5, sigma=1.0, prior_weight=1.0),
+        # Poisson likelihood with the linear bias (rate floored at rho_floor)
+        model.Config(n=8, box=40.0, n_steps=2, lpt_order=2, rsd_axis=1, likelihood="poisson", bias="linear",
+                     bias_b=1.5, nbar_cell=2.0, prior_weight=0.5),
     ]
 
 
-@pytest.mark.parametrize("case", [0, 1, 2])
+@pytest.mark.parametrize("case", [0, 1, 2, 3])
 def test_gradient_brute_force_all_coordinates(table, case):
     """Central finite differences on every one of the 8^3 white-noise
     coordinates against the hand-derived adjoint."""
