@@ -48,6 +48,10 @@ typedef enum {
 
 typedef enum { PM_PREC_F32 = 0, PM_PREC_F64 = 1 } pm_precision;
 typedef enum { PM_LIK_GAUSSIAN = 0, PM_LIK_POISSON = 1 } pm_likelihood;
+/* Galaxy bias model (Sec. 2.2.1 item 4), chosen apart from the likelihood.
+ * AUTO: linear for PM_LIK_GAUSSIAN, power law + sigmoid for PM_LIK_POISSON
+ * (the pairs Sec. 2.2.2 describes; a zero-initialised config gets them). */
+typedef enum { PM_BIAS_AUTO = 0, PM_BIAS_LINEAR = 1, PM_BIAS_POWERLAW_SIGMOID = 2 } pm_bias;
 
 /* Model configuration (Sec. 2.2.1 items 1-5, Sec. 2.2.2). */
 typedef struct {
@@ -57,8 +61,9 @@ typedef struct {
   int32_t rsd_axis;         /* redshift-space shift at a = 1 (Sec. 2.2.1 item 3): -1 none; 0, 1, 2:
                                plane parallel along x, y, z; 3: radial, along the line of sight from
                                `observer` (x_s = x + (p . d) d / (a^2 E), d the unit vector) */
-  int32_t likelihood;       /* PM_LIK_GAUSSIAN: linear bias b, 1/2 sum R (b delta - d)^2 / sigma^2
-                               PM_LIK_POISSON: Eq. galaxy_bias with R and the Poisson likelihood of Sec. 2.2.2 */
+  int32_t likelihood;       /* PM_LIK_GAUSSIAN: 1/2 sum R (f(delta) - d)^2 / sigma^2
+                               PM_LIK_POISSON: sum over R > 0 of lambda - N log lambda, lambda = R nbar g(delta)
+                               (the Poisson likelihood of Sec. 2.2.2 without log N!) */
   int32_t precision;        /* PM_PREC_F32 (FP32 mesh / FFT / particles, FP64 reductions) or PM_PREC_F64 */
   int32_t checkpoint_every; /* 0: pm_adjoint keeps every step's particle state; c > 0: keeps (x, p)
                                every c steps and recomputes the steps in between (same result) */
@@ -67,16 +72,22 @@ typedef struct {
                                a_init = 0.1 with 9 or 18 steps), scale factor from three fixed-point
                                iterations of DistToScaleFactor, linear interpolation between snapshots,
                                radial shift at that scale factor; needs rsd_axis = 3.  0: off */
+  int32_t bias;             /* pm_bias.  Linear: f = b delta (Gaussian), g = max(1 + b delta, rho_floor)
+                               (Poisson; zero derivative below the floor).  Power law + sigmoid (Eq.
+                               galaxy_bias): g = max(1 + delta, rho_floor)^alpha sigmoid(K (delta - delta_th)),
+                               f = nbar g (Gaussian) */
   double box;               /* side of the periodic box, Mpc/h */
   double omega_m;           /* flat LCDM matter density (E(a) and the Poisson source) */
   double a_init;            /* scale factor of the 2LPT initial condition, 0 < a_init < 1 */
-  double bias_b;            /* Gaussian: linear bias b */
+  double bias_b;            /* linear bias: b */
   double sigma;             /* Gaussian: noise standard deviation per cell */
-  double alpha;             /* Poisson: power-law index (paper: 0.7) */
-  double delta_th;          /* Poisson: sigmoid threshold (paper: 1.2) */
-  double K;                 /* Poisson: sigmoid steepness (paper: 3.0) */
-  double nbar_cell;         /* Poisson: normalisation N_G of Eq. galaxy_bias, galaxies per cell */
-  double rho_floor;         /* Poisson: floor on 1 + delta inside the power law (1e-3) */
+  double alpha;             /* power-law bias: index (paper: 0.7) */
+  double delta_th;          /* power-law bias: sigmoid threshold (paper: 1.2) */
+  double K;                 /* power-law bias: sigmoid steepness (paper: 3.0) */
+  double nbar_cell;         /* Poisson, and the Gaussian with the power-law bias: normalisation N_G of
+                               Eq. galaxy_bias, galaxies per cell */
+  double rho_floor;         /* Poisson, and the power-law bias: floor on 1 + delta (power law) or
+                               1 + b delta (linear Poisson rate), 1e-3 */
   double prior_weight;      /* weight w of the Gaussian prior (w/2) sum s^2; 0 = likelihood only */
   double observer[3];       /* rsd_axis = 3: observer position in box coordinates, Mpc/h (may lie
                                outside the box; no particle may sit on it) */
@@ -180,9 +191,9 @@ pm_status pm_force(pm_plan *plan, const void *disp, void *force_out, void *densi
 pm_status pm_evolve(pm_plan *plan, const void *s, void *disp_out, void *mom_out, pm_stream_t stream);
 
 /* Model mean per cell at s, the rate the mock galaxies are drawn from:
- * Poisson: lambda = R nbar (1+delta)^alpha sigmoid(K (delta - delta_th)) (Eq.
- * galaxy_bias times the survey response of Sec. 2.2.1 item 5); Gaussian:
- * b delta.  out: [n^3]. */
+ * Poisson: lambda = R nbar g(delta) (g of the bias model: Eq. galaxy_bias or
+ * the floored linear rate, times the survey response of Sec. 2.2.1 item 5);
+ * Gaussian: f(delta) (b delta, or nbar g(delta)).  out: [n^3]. */
 pm_status pm_expected_counts(pm_plan *plan, const void *s, const void *R, void *out, pm_stream_t stream);
 
 /* ---- annealing: low-resolution stage feeding the full-resolution start (Sec. 3, opening) ---- */
@@ -292,12 +303,16 @@ pm_status pm_count_positive(pm_plan *plan, const void *R, int64_t *count_out, pm
  * order, each sorted descending (plan type).  Ranks break ties by index
  * (lower index = larger).  rng_seed / rng_counter key the reset draws.
  * n_reset_out (nullable host): number of reset values; when non-NULL the call
- * synchronises.  Errors: PM_ERR_INVALID_ARG, PM_ERR_NONFINITE (NaN in s),
- * PM_ERR_CUDA. */
+ * synchronises.  rank_out (nullable, device int32 [n^3], caller-owned): with
+ * PM_ROM_REAL in mode, the rank pi of Sec. 2.3.2 step 1 of every cell with
+ * R > 0 by its value before matching (0 = largest, ties as above; that cell
+ * received targets_real[rank]), -1 for the cells with R <= 0; without
+ * PM_ROM_REAL it is not written.  Errors: PM_ERR_INVALID_ARG,
+ * PM_ERR_NONFINITE (NaN in s), PM_ERR_CUDA. */
 pm_status project_rank_match(pm_plan *plan, void *s_inout, uint32_t mode, const void *R,
                              const void *targets_real, const void *targets_fourier,
                              uint64_t rng_seed, uint64_t rng_counter, int64_t *n_reset_out,
-                             pm_stream_t stream);
+                             int32_t *rank_out, pm_stream_t stream);
 
 /* Projection step only (z-score, then reset |s_hat| > 10 to the same
  * counter-based N(0,1) draws as PM_PROJECT) on n elements of the given

@@ -390,6 +390,18 @@ def likelihood_terms(delta, data, resp, cfg):
     raise ValueError(cfg.likelihood)
 
 
+def model_mean(delta, resp, cfg):
+    """Mean of the data per cell, the rate mock data are drawn from: Poisson
+    R nbar g(delta) on observed cells (zero elsewhere), Gaussian f(delta)."""
+    kind = bias_kind(cfg)
+    if cfg.likelihood == "poisson":
+        g, _ = (_linear_rate if kind == "linear" else _powerlaw_sigmoid)(delta, cfg)
+        return np.where(resp > 0, resp * cfg.nbar_cell * g, 0.0)
+    if kind == "linear":
+        return cfg.bias_b * delta
+    return cfg.nbar_cell * _powerlaw_sigmoid(delta, cfg)[0]
+
+
 def loss(s, cfg, lnk, lnp, data, resp):
     """Total loss = -log L + (w/2) sum s^2.  Returns (loss, parts dict)."""
     disp, mom, ev = evolve(s, cfg, lnk, lnp)

@@ -90,6 +90,18 @@ def rom_real(s, resp, targets_desc):
     return out.reshape(np.shape(s))
 
 
+def rom_real_ranks(s, resp):
+    """pi_i of Sec. 2.3.2 step 1 for real-space matching: each cell's
+    descending rank among the cells with R(q) > 0 (0 = largest; ties: the
+    lower flat index first), -1 for the cells outside that region."""
+    x = np.asarray(s, dtype=np.float64).reshape(-1)
+    sel = np.nonzero(np.asarray(resp).reshape(-1) > 0)[0]
+    order = np.argsort(-x[sel], kind="stable")
+    rank = np.full(x.size, -1, dtype=np.int64)
+    rank[sel[order]] = np.arange(sel.size)
+    return rank.reshape(np.shape(s))
+
+
 N_BINS = 100
 K_MIN = 0.1
 

@@ -16,6 +16,7 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_UNSUPPORTED", 3: "PM_E
           7: "PM_ERR_DEVICE_STATUS"}
 PM_PREC_F32, PM_PREC_F64 = 0, 1
 PM_LIK_GAUSSIAN, PM_LIK_POISSON = 0, 1
+PM_BIAS_AUTO, PM_BIAS_LINEAR, PM_BIAS_POWERLAW_SIGMOID = 0, 1, 2
 PM_PROJECT, PM_ROM_FOURIER, PM_ROM_REAL = 1, 2, 4
 
 
@@ -29,7 +30,7 @@ class pm_config(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("lpt_order", ctypes.c_int32),
         ("rsd_axis", ctypes.c_int32), ("likelihood", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("checkpoint_every", ctypes.c_int32), ("lightcone", ctypes.c_int32),
+        ("checkpoint_every", ctypes.c_int32), ("lightcone", ctypes.c_int32), ("bias", ctypes.c_int32),
         ("box", ctypes.c_double), ("omega_m", ctypes.c_double), ("a_init", ctypes.c_double),
         ("bias_b", ctypes.c_double), ("sigma", ctypes.c_double), ("alpha", ctypes.c_double),
         ("delta_th", ctypes.c_double), ("K", ctypes.c_double), ("nbar_cell", ctypes.c_double),
@@ -80,7 +81,7 @@ SIGNATURES = {
     "pm_profile_read": (_I32, [_P, _I32, _DP, _I64P, _DP, _DP, _DP]),
     "pm_rom_fourier_counts": (_I32, [_P, _I64P]),
     "pm_count_positive": (_I32, [_P, _P, _I64P, _P]),
-    "project_rank_match": (_I32, [_P, _P, _U32, _P, _P, _P, _U64, _U64, _I64P, _P]),
+    "project_rank_match": (_I32, [_P, _P, _U32, _P, _P, _P, _U64, _U64, _I64P, _P, _P]),
     "pm_project_noalloc": (_I32, [_I64, _I32, _P, _U64, _U64, _I64P, _P]),
     "lbfgs_workspace_bytes": (_I32, [_I64, _I32, _I32, _SZP]),
     "lbfgs_create": (_I32, [_I64, _I32, _I32, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),

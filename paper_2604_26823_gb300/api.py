@@ -63,6 +63,7 @@ class Config:
     lpt_order: int = 2
     rsd_axis: int = -1                # -1 none, 0..2 plane parallel, 3 radial from `observer`
     likelihood: str = "gaussian"      # "gaussian" | "poisson"
+    bias: str = "auto"                # "auto" (gaussian: linear, poisson: power law) | "linear" | "powerlaw_sigmoid"
     precision: str = "f32"            # "f32" | "f64"
     checkpoint_every: int = 0
     omega_m: float = 0.25
@@ -82,6 +83,8 @@ class Config:
         c = L.pm_config()
         c.n, c.n_steps, c.lpt_order, c.rsd_axis = self.n, self.n_steps, self.lpt_order, self.rsd_axis
         c.likelihood = {"gaussian": L.PM_LIK_GAUSSIAN, "poisson": L.PM_LIK_POISSON}[self.likelihood]
+        c.bias = {"auto": L.PM_BIAS_AUTO, "linear": L.PM_BIAS_LINEAR,
+                  "powerlaw_sigmoid": L.PM_BIAS_POWERLAW_SIGMOID}[self.bias]
         c.precision = {"f32": L.PM_PREC_F32, "f64": L.PM_PREC_F64}[self.precision]
         c.checkpoint_every = self.checkpoint_every
         c.lightcone = 1 if self.lightcone else 0
@@ -238,7 +241,8 @@ def pm_evolve(plan, s, stream=None):
 
 
 def pm_expected_counts(plan, s, R, out=None, stream=None):
-    """Model mean per cell (Poisson rate or b delta) at s."""
+    """Model mean per cell at s: the Poisson rate R nbar g(delta), or the
+    Gaussian's biased field f(delta)."""
     out = plan.empty() if out is None else out
     L.check(plan.call("pm_expected_counts", plan.handle, plan.mesh(s, "s"), plan.mesh(R, "R"), plan.mesh(out, "out"),
                                         _stream(stream, plan.device)), "pm_expected_counts")
@@ -364,9 +368,11 @@ def pm_count_positive(plan, R, stream=None):
 
 
 def project_rank_match(plan, s_inout, mode, R=None, targets_real=None, targets_fourier=None, seed=0,
-                       counter=0, stream=None):
+                       counter=0, stream=None, rank_out=None):
     """In place: Fourier matching, real-space matching, projection (by mode bits).
-    Returns the number of reset values."""
+    Returns the number of reset values.  rank_out (optional int32 CUDA tensor
+    of n^3 elements): with real-space matching, each cell's rank among the
+    R > 0 cells before matching, -1 elsewhere."""
     nres = ctypes.c_int64()
     # the library reads exactly one target per matched value: refuse lists of
     # another length before the call
@@ -378,9 +384,11 @@ def project_rank_match(plan, s_inout, mode, R=None, targets_real=None, targets_f
     if targets_fourier is not None and int(mode) & L.PM_ROM_FOURIER:
         need = int(pm_rom_fourier_counts(plan).sum())
         tf = _ptr(targets_fourier, plan.dtype, need, "targets_fourier", plan.device)
+    rk = None if rank_out is None else _ptr(rank_out, torch.int32, plan.ncell, "rank_out", plan.device)
     L.check(plan.call("project_rank_match", plan.handle, plan.mesh(s_inout, "s"), int(mode),
                                         plan.mesh(R, "R") if R is not None else None, tr, tf,
-                                        int(seed), int(counter), ctypes.byref(nres), _stream(stream, plan.device)),
+                                        int(seed), int(counter), ctypes.byref(nres), rk,
+                                        _stream(stream, plan.device)),
             "project_rank_match")
     return nres.value
 

@@ -40,7 +40,8 @@ pm_status pm_validate_config(const pm_config *c) {
   }
   if (c->n_steps < 1 || c->n_steps > 1000 || (c->lpt_order != 1 && c->lpt_order != 2) || c->rsd_axis < -1 ||
       c->rsd_axis > 3 || (c->likelihood != PM_LIK_GAUSSIAN && c->likelihood != PM_LIK_POISSON) ||
-      (c->precision != PM_PREC_F32 && c->precision != PM_PREC_F64) || c->checkpoint_every < 0) {
+      (c->precision != PM_PREC_F32 && c->precision != PM_PREC_F64) || c->checkpoint_every < 0 ||
+      (c->bias != PM_BIAS_AUTO && c->bias != PM_BIAS_LINEAR && c->bias != PM_BIAS_POWERLAW_SIGMOID)) {
     pm::set_error("invalid enum / step count / checkpoint setting");
     return PM_ERR_INVALID_ARG;
   }
@@ -69,8 +70,9 @@ pm_status pm_validate_config(const pm_config *c) {
     pm::set_error("Gaussian likelihood needs sigma > 0");
     return PM_ERR_INVALID_ARG;
   }
-  if (c->likelihood == PM_LIK_POISSON && (!(c->nbar_cell > 0) || !(c->rho_floor > 0))) {
-    pm::set_error("Poisson likelihood needs nbar_cell > 0 and rho_floor > 0");
+  const bool powerlaw = c->bias == PM_BIAS_POWERLAW_SIGMOID || (c->bias == PM_BIAS_AUTO && c->likelihood == PM_LIK_POISSON);
+  if ((c->likelihood == PM_LIK_POISSON || powerlaw) && (!(c->nbar_cell > 0) || !(c->rho_floor > 0))) {
+    pm::set_error("the Poisson likelihood and the power-law bias need nbar_cell > 0 and rho_floor > 0");
     return PM_ERR_INVALID_ARG;
   }
   return PM_OK;
@@ -496,7 +498,7 @@ pm_status pm_count_positive(pm_plan *plan, const void *R, int64_t *count_out, pm
 
 pm_status project_rank_match(pm_plan *plan, void *s_inout, uint32_t mode, const void *R, const void *targets_real,
                              const void *targets_fourier, uint64_t rng_seed, uint64_t rng_counter,
-                             int64_t *n_reset_out, pm_stream_t stream) {
+                             int64_t *n_reset_out, int32_t *rank_out, pm_stream_t stream) {
   if (!s_inout || (mode & ~7u) || ((mode & PM_ROM_REAL) && (!R || !targets_real)) ||
       ((mode & PM_ROM_FOURIER) && !targets_fourier)) {
     pm::set_error("invalid project_rank_match arguments");
@@ -507,7 +509,8 @@ pm_status project_rank_match(pm_plan *plan, void *s_inout, uint32_t mode, const 
     pm::rom::Rom<T> r{E};
     pm_status st = PM_OK;
     if (mode & PM_ROM_FOURIER) st = r.fourier((T *)s_inout, (const T *)targets_fourier);
-    if (!st && (mode & PM_ROM_REAL)) st = r.real((T *)s_inout, (const T *)R, (const T *)targets_real);
+    if (!st && (mode & PM_ROM_REAL))
+      st = r.real((T *)s_inout, (const T *)R, (const T *)targets_real, reinterpret_cast<int *>(rank_out));
     if (!st && (mode & PM_PROJECT)) st = r.project((T *)s_inout, rng_seed, rng_counter, n_reset_out);
     if (!st && !(mode & PM_PROJECT)) {
       const cudaError_t e = cudaStreamSynchronize(E.st);

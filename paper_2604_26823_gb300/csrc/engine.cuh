@@ -649,17 +649,25 @@ template <typename T> struct Engine {
     return deposit(fsrc);
   }
 
-  pm_status loss_terms(const T *s, const T *data, const T *R, const T *cot, double lw, bool want_dbar,
-                       T *delta_out) {
+  // likelihood and bias parameters of the kernels, the bias model resolved
+  pw::LossParams loss_params() const {
     pw::LossParams lp{};
     lp.lik = cfg.likelihood;
+    lp.bias = cfg.bias == PM_BIAS_LINEAR || (cfg.bias == PM_BIAS_AUTO && cfg.likelihood == PM_LIK_GAUSSIAN) ? 0 : 1;
     lp.b = cfg.bias_b;
-    lp.inv_s2 = 1.0 / (cfg.sigma * cfg.sigma);
+    lp.inv_s2 = cfg.likelihood == PM_LIK_GAUSSIAN ? 1.0 / (cfg.sigma * cfg.sigma) : 0.0;
     lp.alpha = cfg.alpha;
     lp.delta_th = cfg.delta_th;
     lp.K = cfg.K;
     lp.nbar = cfg.nbar_cell;
     lp.rho_floor = cfg.rho_floor;
+    lp.lw = 1.0;
+    return lp;
+  }
+
+  pm_status loss_terms(const T *s, const T *data, const T *R, const T *cot, double lw, bool want_dbar,
+                       T *delta_out) {
+    pw::LossParams lp = loss_params();
     lp.lw = lw;
     const double lw_io = (2 + (want_dbar ? 1 : 0) + (delta_out ? 1 : 0)) * sizeof(T);
     ProfScope ps(prof, P_LOSS, st, (double)M * (sizeof(T) + lw_io), (double)M * (8 + lw_io));
@@ -870,18 +878,10 @@ template <typename T> struct Engine {
     return PM_OK;
   }
 
-  // model mean per cell: Poisson lambda = R nbar (1+delta)^alpha sigmoid(K(delta - delta_th)),
-  // Gaussian b delta
+  // model mean per cell: Poisson lambda = R nbar g(delta), Gaussian f(delta)
   pm_status expected_counts(const T *s, const T *R, T *out) {
     PM_TRY(forward_to_density(s, false));
-    pw::LossParams lp{};
-    lp.lik = cfg.likelihood;
-    lp.b = cfg.bias_b;
-    lp.alpha = cfg.alpha;
-    lp.delta_th = cfg.delta_th;
-    lp.K = cfg.K;
-    lp.nbar = cfg.nbar_cell;
-    lp.rho_floor = cfg.rho_floor;
+    const pw::LossParams lp = loss_params();
     ::pm::note_launch();
     pw::k_expected<T><<<grid_for(M, 256), 256, 0, st>>>(lp, fx, fx_exp, R, out, M);
     PM_LAUNCH_CHECK();

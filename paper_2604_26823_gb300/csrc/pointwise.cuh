@@ -136,10 +136,33 @@ __global__ void k_amplitude(T *amp, int n, double kf, double inv_cell3, const do
 
 struct LossParams {
   int lik;           // 0 gaussian, 1 poisson
-  double b, inv_s2;  // gaussian
-  double alpha, delta_th, K, nbar, rho_floor;  // poisson
+  int bias;          // 0 linear, 1 power law + sigmoid
+  double b, inv_s2;  // linear bias; gaussian 1 / sigma^2
+  double alpha, delta_th, K, nbar, rho_floor;  // power law + sigmoid; normalisation and floor
   double lw;         // loss weight for the derivative
 };
+
+// Galaxy density per unit nbar, g(delta), and dg/d delta (Sec. 2.2.1 item 4).
+// Linear: max(1 + b delta, rho_floor), derivative b above the floor.  Power law
+// + sigmoid (Eq. galaxy_bias): max(1+delta, rho_floor)^alpha sigmoid(K (delta -
+// delta_th)), the power-law factor's derivative zero below the floor.  onep is
+// 1 + delta rounded once from the exact density.
+template <typename T>
+__device__ __forceinline__ void bias_rate(const LossParams &lp, T delta, T onep, T &g, T &dg) {
+  const T fl = (T)lp.rho_floor;
+  if (lp.bias == 0) {
+    const T base = T(1) + (T)lp.b * delta;
+    g = base > fl ? base : fl;
+    dg = base > fl ? (T)lp.b : T(0);
+  } else {
+    const T base = onep > fl ? onep : fl;
+    const T sg = T(1) / (T(1) + exp(-(T)lp.K * (delta - (T)lp.delta_th)));
+    const T pw = pow(base, (T)lp.alpha);
+    g = pw * sg;
+    const T dpow = onep > fl ? (T)lp.alpha * pw / base : T(0);
+    dg = dpow * sg + pw * (T)lp.K * sg * (T(1) - sg);
+  }
+}
 
 // Per cell: delta = rho - 1 from the fixed-point density, the likelihood term
 // (block partials in FP64), dbar = lw * d(term)/d delta (+ cot), delta_out.
@@ -165,19 +188,24 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
     const T r = resp[i];
     T g = T(0);
     if (lp.lik == 0) {
-      const T res = (T)lp.b * delta - data[i];
+      // residual of the biased field: b delta, or nbar g(delta)
+      T f = (T)lp.b * delta, df = (T)lp.b;
+      if (lp.bias != 0) {
+        T gb, dgb;
+        bias_rate(lp, delta, onep, gb, dgb);
+        f = (T)lp.nbar * gb;
+        df = (T)lp.nbar * dgb;
+      }
+      const T res = f - data[i];
       acc.add(T(0.5) * r * res * res * (T)lp.inv_s2);
-      g = r * (T)lp.b * res * (T)lp.inv_s2;
+      g = r * df * res * (T)lp.inv_s2;
     } else if (r > T(0)) {
-      const T base = onep > (T)lp.rho_floor ? onep : (T)lp.rho_floor;
-      const T sg = T(1) / (T(1) + exp(-(T)lp.K * (delta - (T)lp.delta_th)));
-      const T pw = pow(base, (T)lp.alpha);
-      const T lam = r * (T)lp.nbar * pw * sg;
+      T gb, dgb;
+      bias_rate(lp, delta, onep, gb, dgb);
+      const T lam = r * (T)lp.nbar * gb;
       const T cnt = data[i];
       acc.add(lam - cnt * log(lam));
-      const T dpow = onep > (T)lp.rho_floor ? (T)lp.alpha * pw / base : T(0);
-      const T dg = dpow * sg + pw * (T)lp.K * sg * (T(1) - sg);
-      g = r * (T)lp.nbar * dg * (T(1) - cnt / lam);
+      g = r * (T)lp.nbar * dgb * (T(1) - cnt / lam);
     }
     if (dbar) dbar[i] = (T)lp.lw * g + (cot ? cot[i] : T(0));
   }
@@ -199,12 +227,12 @@ __global__ void k_expected(LossParams lp, const long long *__restrict__ rho, con
     delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
     onep = scalbn(__ll2double_rn(rho[i]), e);
   }
+  T gb = T(0), dgb = T(0);
+  if (lp.lik != 0 || lp.bias != 0) bias_rate(lp, delta, onep, gb, dgb);
   if (lp.lik == 0) {
-    out[i] = (T)lp.b * delta;
+    out[i] = lp.bias == 0 ? (T)lp.b * delta : (T)lp.nbar * gb;
   } else {
-    const T base = onep > (T)lp.rho_floor ? onep : (T)lp.rho_floor;
-    const T sg = T(1) / (T(1) + exp(-(T)lp.K * (delta - (T)lp.delta_th)));
-    out[i] = resp[i] > T(0) ? resp[i] * (T)lp.nbar * pow(base, (T)lp.alpha) * sg : T(0);
+    out[i] = resp[i] > T(0) ? resp[i] * (T)lp.nbar * gb : T(0);
   }
 }
 

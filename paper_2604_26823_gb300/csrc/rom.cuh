@@ -112,13 +112,16 @@ __global__ void k_real_keys(const T *__restrict__ s, const T *__restrict__ R, in
   vals[i] = (unsigned int)i;
 }
 
-// s[cell of the j-th sorted entry] = targets[j] for the R > 0 entries.
+// s[cell of the j-th sorted entry] = targets[j] for the R > 0 entries, and
+// that cell's rank j (when rank is given; the other cells keep -1).
 template <typename T, typename K>
 __global__ void k_real_assign(const K *__restrict__ keys, const unsigned int *__restrict__ vals, int64_t n,
-                              const T *__restrict__ targets, T *s) {
+                              const T *__restrict__ targets, T *s, int *rank) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n || keys[j] == ~K(0)) return;
-  s[vals[j]] = targets[j];
+  const unsigned int c = vals[j];
+  s[c] = targets[j];
+  if (rank) rank[c] = (int)j;
 }
 
 // Fourier mode selection: canonical member of its conjugate pair, not its
@@ -247,8 +250,9 @@ template <typename T> struct Rom {
   }
   int64_t nmax() const { return 2 * E.S; }
 
-  pm_status real(T *s, const T *R, const T *targets) {
+  pm_status real(T *s, const T *R, const T *targets, int *rank) {
     const int64_t n = E.M;
+    if (rank) PM_CUDA_TRY(cudaMemsetAsync(rank, 0xff, (size_t)n * sizeof(int), E.st));  // -1 everywhere
     SortWs w = ws(nmax());
     ::pm::note_launch();
     k_real_keys<T, K><<<grid_for(n, 256), 256, 0, E.st>>>(s, R, n, w.k1, w.v1);
@@ -257,7 +261,7 @@ template <typename T> struct Rom {
     unsigned int *vr;
     PM_CUDA_TRY(sortk::radix_sort<K>(w.k1, w.v1, w.k2, w.v2, n, 8 * (int)sizeof(K), w.hist, w.totals, E.st, &kr, &vr));
     ::pm::note_launch();
-    k_real_assign<T, K><<<grid_for(n, 256), 256, 0, E.st>>>(kr, vr, n, targets, s);
+    k_real_assign<T, K><<<grid_for(n, 256), 256, 0, E.st>>>(kr, vr, n, targets, s, rank);
     PM_LAUNCH_CHECK();
     return PM_OK;
   }

@@ -37,6 +37,14 @@ CASES = {
     "lightcone32": dict(n=32, box=128.0, n_steps=9, lpt_order=2, rsd_axis=3, lightcone=True,
                         observer=(64.0, 64.0, -260.0), likelihood="gaussian", bias_b=1.5, sigma=1.0,
                         prior_weight=1.0),
+    # each bias model with the other likelihood, 32^3 in 128 Mpc/h, 5 steps:
+    # masked Poisson with the linear bias (rate max(1 + b delta, rho_floor)),
+    # RSD along y; Gaussian on nbar times the power law + sigmoid
+    "poislin32": dict(n=32, box=128.0, n_steps=5, lpt_order=2, rsd_axis=1, likelihood="poisson", bias="linear",
+                      bias_b=1.5, nbar_cell=0.5, rho_floor=1e-3, prior_weight=1.0),
+    "gausspl32": dict(n=32, box=128.0, n_steps=5, lpt_order=2, rsd_axis=-1, likelihood="gaussian",
+                      bias="powerlaw_sigmoid", sigma=1.0, nbar_cell=2.0, alpha=0.7, delta_th=1.2, K=3.0,
+                      rho_floor=1e-3, prior_weight=1.0),
     # Zel'dovich start, RSD along x, 16^3 (single-tile meshes)
     "tiny": dict(n=16, box=48.0, n_steps=3, lpt_order=1, rsd_axis=0, likelihood="gaussian",
                  bias_b=1.2, sigma=0.8, prior_weight=0.5),
@@ -44,7 +52,8 @@ CASES = {
 
 
 def oracle_config(kw):
-    keys = ("n", "box", "n_steps", "lpt_order", "rsd_axis", "observer", "lightcone", "likelihood", "bias_b", "sigma",
+    keys = ("n", "box", "n_steps", "lpt_order", "rsd_axis", "observer", "lightcone", "likelihood", "bias", "bias_b",
+            "sigma",
             "alpha",
             "delta_th", "K", "nbar_cell", "rho_floor", "prior_weight")
     return OM.Config(**{k: kw[k] for k in keys if k in kw})

@@ -3,6 +3,8 @@ declares; host-side validation and host coefficients (no GPU needed)."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -35,10 +37,27 @@ def test_exports_every_declared_symbol(lib):
     assert set(names) == set(_lib.SIGNATURES), set(names) ^ set(_lib.SIGNATURES)
 
 
-def test_config_struct_layout_matches_header(lib):
+def test_config_struct_layout_matches_header(lib, tmp_path):
+    """The binding's pm_config has the size and field offsets a C compiler
+    gives the header's struct."""
     from paper_2604_26823_gb300 import _lib
-    assert ctypes.sizeof(_lib.pm_config) == 8 * 4 + 14 * 8
     assert lib.pm_version().decode().startswith("mujica-pm")
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in _lib.pm_config._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"mujica_pm.h\"\nint main(void) {\n"
+                   '  printf("size %zu\\n", sizeof(pm_config));\n'
+                   + "".join(f'  printf("{f} %zu\\n", offsetof(pm_config, {f}));\n' for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(_lib.pm_config)
+    for f in fields:
+        assert int(out[f]) == getattr(_lib.pm_config, f).offset, f
 
 
 def test_validation_errors_without_gpu(lib):
@@ -50,6 +69,14 @@ def test_validation_errors_without_gpu(lib):
     cfg = api.Config(n=32, box=-1.0).to_c()
     assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 1
     cfg = api.Config(n=32, box=128.0, likelihood="poisson", nbar_cell=0.0).to_c()
+    assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 1
+    cfg = api.Config(n=32, box=128.0, bias="powerlaw_sigmoid", nbar_cell=0.0).to_c()
+    assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 1
+    assert b"power-law bias" in lib.pm_last_error()
+    cfg = api.Config(n=32, box=128.0, bias="linear", nbar_cell=0.0).to_c()   # Gaussian, linear: no nbar
+    assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 0
+    cfg = api.Config(n=32, box=128.0).to_c()
+    cfg.bias = 3
     assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 1
     cfg = api.Config(n=32, box=128.0).to_c()
     assert lib.pm_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nb)) == 0

@@ -125,7 +125,8 @@ def test_evolve(api, name, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-@pytest.mark.parametrize("name", ["tiny", "small", "poisson64", "rsd128", "radial64", "lightcone32"])
+@pytest.mark.parametrize("name", ["tiny", "small", "poisson64", "rsd128", "radial64", "lightcone32", "poislin32",
+                                  "gausspl32"])
 def test_forward_loss_and_density(api, name, prec):
     plan = plan_for(api, name, prec)
     s, data, resp = case_inputs(name)
@@ -140,7 +141,8 @@ def test_forward_loss_and_density(api, name, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-@pytest.mark.parametrize("name", ["tiny", "small", "poisson64", "rsd128", "radial64", "lightcone32"])
+@pytest.mark.parametrize("name", ["tiny", "small", "poisson64", "rsd128", "radial64", "lightcone32", "poislin32",
+                                  "gausspl32"])
 def test_gradient(api, name, prec):
     plan = plan_for(api, name, prec)
     s, data, resp = case_inputs(name)
@@ -169,6 +171,20 @@ def test_gradient(api, name, prec):
         print(f"gradient {name} f64: GPU rel L2 {err:.3e} cos {cos:.12f}")
     assert err < bound, (err, bound)
     assert cos > 1 - (1e-5 if prec == "f32" else 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("name", ["small", "poisson64", "poislin32", "gausspl32"])
+def test_expected_counts(api, name, prec):
+    """The model mean (the mock rate) of each likelihood and bias model."""
+    plan = plan_for(api, name, prec)
+    s, _, resp = case_inputs(name)
+    mu = api.pm_expected_counts(plan, dev(s, prec), dev(resp, prec)).cpu().numpy()
+    _, _, info = oracle_gradient(name)
+    ref = OM.model_mean(info["delta"], resp, oracle_config(CASES[name]))
+    assert rel_l2(mu, ref) < TOL[prec], rel_l2(mu, ref)
+    if CASES[name]["likelihood"] == "poisson":
+        assert np.all(mu[resp == 0] == 0)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])

@@ -170,9 +170,12 @@ def test_real_rom_bit_exact_over_2_20_keys(api, prec):
     assert cnt == int((resp > 0).sum()) and cnt > (1 << 20)
     t = inputs.sorted_normal_targets(cnt, 4)
     x = dev(s, prec)
-    api.project_rank_match(plan, x, api.L.PM_ROM_REAL, R=dev(resp, prec), targets_real=dev(t, prec))
+    rank = torch.zeros(n ** 3, dtype=torch.int32, device="cuda")
+    api.project_rank_match(plan, x, api.L.PM_ROM_REAL, R=dev(resp, prec), targets_real=dev(t, prec), rank_out=rank)
     ref = OP.rom_real(s.astype(np.float64), resp.astype(np.float64), t.astype(np.float64))
     np.testing.assert_array_equal(x.cpu().numpy().astype(np.float64), ref)
+    np.testing.assert_array_equal(rank.cpu().numpy().astype(np.int64),
+                                  OP.rom_real_ranks(s.astype(np.float64), resp).reshape(-1))
 
 
 def _q(x, prec):

@@ -74,6 +74,24 @@ def test_likelihood_matches_library_densities(lik, bias):
         assert below.sum() > 10 and np.all(grad[below] == 0)
 
 
+@pytest.mark.parametrize("lik,bias", [("gaussian", "linear"), ("gaussian", "powerlaw_sigmoid"),
+                                      ("poisson", "linear"), ("poisson", "powerlaw_sigmoid")])
+def test_model_mean(lik, bias):
+    """The mock rate: R times the mean of Eq. galaxy_bias (or the linear
+    model) for the Poisson, the biased field for the Gaussian; the Gaussian
+    likelihood vanishes at data equal to it."""
+    cfg = dataclasses.replace(CFG, likelihood=lik, bias=bias)
+    delta, resp = _fields(1024, 11)
+    mu = model.model_mean(delta, resp, cfg)
+    if lik == "poisson":
+        np.testing.assert_allclose(mu, np.where(resp > 0, resp * _mean(delta, cfg, bias), 0.0), rtol=1e-14)
+    else:
+        ref = cfg.bias_b * delta if bias == "linear" else _mean(delta, cfg, bias)
+        np.testing.assert_allclose(mu, ref, rtol=1e-14)
+        val, grad = model.likelihood_terms(delta, mu, resp, cfg)
+        assert val == 0.0 and np.all(grad == 0.0)
+
+
 def test_auto_bias_is_the_papers_pairing():
     delta, resp = _fields(512, 7)
     data = np.random.default_rng(8).poisson(resp).astype(np.float64)

@@ -113,6 +113,26 @@ def test_rom_real_touches_only_selected_cells():
     np.testing.assert_array_equal(np.sort(out[sel]), np.sort(t))
 
 
+def test_rom_real_ranks_brute_force():
+    """Rank by direct counting: the number of selected cells with a larger
+    value, or an equal value at a lower index."""
+    n = 8
+    s = inputs.white_noise(n, 6).astype(np.float64).reshape(-1)
+    s[10:40] = 0.25                     # ties
+    resp = inputs.uniform_field(n, 7, -1.0, 1.0).astype(np.float64).reshape(-1)
+    rank = P.rom_real_ranks(s, resp)
+    sel = np.nonzero(resp > 0)[0]
+    for i in range(s.size):
+        if resp[i] > 0:
+            assert rank[i] == sum(1 for j in sel if s[j] > s[i] or (s[j] == s[i] and j < i))
+        else:
+            assert rank[i] == -1
+    # real-space matching puts the rank-r target at the rank-r cell
+    t = inputs.sorted_normal_targets(sel.size, 8).astype(np.float64)
+    out = P.rom_real(s, resp, t)
+    np.testing.assert_array_equal(out[sel], t[rank[sel]])
+
+
 def test_fourier_mode_selection_brute_force():
     # canonical half-space modes by direct enumeration of conjugate pairs
     n, box = 8, 20.0
