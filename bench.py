@@ -500,7 +500,7 @@ def run_ours(args, ws, rank, local):
     if not args.no_fp64:
         del plan
         torch.cuda.empty_cache()
-        fma = {"f32_tflops": api.pm_fma_rate("f32", 16384), "f64_tflops": api.pm_fma_rate("f64", 4096)}
+        fma = {"f32_tflops": api.pm_fma_rate("f32", 65536), "f64_tflops": api.pm_fma_rate("f64", 8192)}
         plan64 = api.Plan(config(api, nbar_cell, "f64"), lnk, lnp)
         d64 = lambda x: torch.as_tensor(x).to(device="cuda", dtype=torch.float64)
         st64 = api.LBFGS(N ** 3, m=10, precision="f64")

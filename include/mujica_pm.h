@@ -107,7 +107,8 @@ int64_t pm_launch_count(void);
  * (diagnostics: the arithmetic ceiling of the all-FP64 path, no counterpart in
  * the paper).  One launch of 8 blocks per SM x 256 threads, each running 8
  * independent FMA chains of `iters` steps (1 <= iters <= 1e6), timed with CUDA
- * events on the stream; *tflops_out = 2 x FMAs / time in TFLOP/s.  scratch:
+ * events on the stream after an untimed one-step launch of the same kernel;
+ * *tflops_out = 2 x FMAs / time in TFLOP/s.  scratch:
  * device buffer of >= 8 bytes, written only in a case the arithmetic never
  * reaches (it keeps the chains live).  Synchronises.  Errors:
  * PM_ERR_INVALID_ARG, PM_ERR_CUDA. */

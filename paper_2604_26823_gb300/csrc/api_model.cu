@@ -99,12 +99,19 @@ pm_status pm_fma_rate(int32_t precision, int64_t iters, void *scratch, double *t
   PM_CUDA_TRY(cudaEventCreate(&e0));
   PM_CUDA_TRY(cudaEventCreate(&e1));
   float ms = 0.f;
-  cudaError_t err = cudaEventRecord(e0, s);
-  ::pm::note_launch();
-  if (precision == PM_PREC_F32)
-    pm::pw::k_fma_probe<float><<<grid, block, 0, s>>>(iters, (float *)scratch);
-  else
-    pm::pw::k_fma_probe<double><<<grid, block, 0, s>>>(iters, (double *)scratch);
+  // one untimed launch first: the first launch of a kernel in a process loads
+  // its module on the host, which would otherwise open a gap between the events
+  auto launch = [&](int64_t it) {
+    ::pm::note_launch();
+    if (precision == PM_PREC_F32)
+      pm::pw::k_fma_probe<float><<<grid, block, 0, s>>>(it, (float *)scratch);
+    else
+      pm::pw::k_fma_probe<double><<<grid, block, 0, s>>>(it, (double *)scratch);
+  };
+  launch(1);
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+  if (err == cudaSuccess) launch(iters);
   if (err == cudaSuccess) err = cudaGetLastError();
   if (err == cudaSuccess) err = cudaEventRecord(e1, s);
   if (err == cudaSuccess) err = cudaEventSynchronize(e1);
