@@ -412,15 +412,12 @@ template <typename T> struct Engine {
   pm_status x1toM(const C *in, const int *out_slots, const fft::MultDesc *m, int count) {
     fft::XArgs1 a{};
     a.in = in;
-    for (int i = 0; i < count; ++i) {
-      a.out[i] = slot(out_slots[i]);
-      a.mult.m[i] = m[i];
-    }
-    a.mult.count = count;
+    for (int i = 0; i < count; ++i) a.out[i] = slot(out_slots[i]);
+    a.plan = fft::make_xplan(m, count);
     a.amp = amp;
     a.kf = kf;
     ProfScope ps(prof, P_X_FUSED, st, (double)(1 + count) * S * sizeof(C), -1.0,
-                 fft_flops((double)(1 + count) * n * H, n));
+                 fft_flops((double)(1 + a.plan.nparts) * n * H, n));
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
       auto kern = fft::k_x_1toM<T, NN, CC::B, CC::NT, CC::MINB_X>;
@@ -433,16 +430,13 @@ template <typename T> struct Engine {
   }
   pm_status xMto1(const int *in_slots, int out_slot, const fft::MultDesc *m, int count) {
     fft::XArgsN a{};
-    for (int i = 0; i < count; ++i) {
-      a.in[i] = slot(in_slots[i]);
-      a.mult.m[i] = m[i];
-    }
-    a.mult.count = count;
+    for (int i = 0; i < count; ++i) a.in[i] = slot(in_slots[i]);
+    a.plan = fft::make_xplan(m, count);
     a.out = slot(out_slot);
     a.amp = amp;
     a.kf = kf;
     ProfScope ps(prof, P_X_FUSED, st, (double)(1 + count) * S * sizeof(C), -1.0,
-                 fft_flops((double)(1 + count) * n * H, n));
+                 fft_flops((double)(1 + a.plan.nparts) * n * H, n));
     PM_DISPATCH_N(n, {
       using CC = CCfg<T, NN>;
       auto kern = fft::k_x_Mto1<T, NN, CC::B, CC::NT, CC::MINB_X>;

@@ -155,10 +155,53 @@ struct MultDesc {
   int d1, d2, flags, cube;
   double gauss;
 };
-struct MultSet {
-  MultDesc m[9];
-  int count;
+// The x pass sees one column (k_y, k_z fixed) at a time, so each multiplier
+// factors as h_o(k) = X_p(k) C_o(k_y, k_z): a part X_p that varies along the
+// column (amplitude, 1/k^2, Gaussian, cube masks, derivatives along x) and a
+// per-column constant C_o (scale, derivatives along y and z; with nd
+// derivatives in all, (i)^nd = (i)^nx (i)^nc).  Multipliers with the same X_p
+// share one transform: IFFT_x(h_o X) = C_o IFFT_x(X_p X), and
+// sum_i h_i FFT_x(in_i) = sum_p X_p FFT_x(sum_{i in p} C_i in_i).
+struct XPlan {
+  MultDesc xpart[9];  // distinct column-varying parts (scale 1, x derivatives only)
+  MultDesc col[9];    // per spectrum: scale and y / z derivatives (no other flag but M_CONJ)
+  int part_of[9];     // spectrum -> its part
+  int nparts, count;
 };
+
+inline XPlan make_xplan(const MultDesc *m, int count) {
+  XPlan p{};
+  p.count = count;
+  for (int o = 0; o < count; ++o) {
+    const int ds[2] = {m[o].d1, m[o].d2};
+    int nx = 0, dc[2] = {-1, -1}, nc = 0;
+    for (int d : ds) {
+      if (d == 0) ++nx;
+      else if (d > 0) dc[nc++] = d;
+    }
+    MultDesc x = m[o];
+    x.scale = 1.0;
+    x.d1 = nx >= 1 ? 0 : -1;
+    x.d2 = nx >= 2 ? 0 : -1;
+    if (nx != 1) x.flags &= ~M_CONJ;  // the sign only enters with one imaginary unit
+    MultDesc c{};
+    c.scale = m[o].scale;
+    c.d1 = dc[0];
+    c.d2 = dc[1];
+    c.flags = nc == 1 ? (m[o].flags & M_CONJ) : 0;
+    c.cube = 0;
+    c.gauss = 0.0;
+    int q = 0;
+    for (; q < p.nparts; ++q) {
+      const MultDesc &y = p.xpart[q];
+      if (y.flags == x.flags && y.d1 == x.d1 && y.d2 == x.d2 && y.cube == x.cube && y.gauss == x.gauss) break;
+    }
+    if (q == p.nparts) p.xpart[p.nparts++] = x;
+    p.part_of[o] = q;
+    p.col[o] = c;
+  }
+  return p;
+}
 
 template <typename T> struct ModeK {
   T k[3];   // k_i, zero at that axis' Nyquist index
@@ -368,7 +411,7 @@ __global__ void __launch_bounds__(NT) k_col(const cx<T> *in, cx<T> *out, int64_t
 struct XArgs1 {  // one input spectrum -> up to 9 output spectra
   const void *in;
   void *out[9];
-  MultSet mult;
+  XPlan plan;
   const void *amp;  // IC amplitude on the half spectrum (or null)
   double kf;        // 2 pi / L
   int64_t bstride;  // batch stride of the input (and outputs) in complex elements
@@ -376,12 +419,13 @@ struct XArgs1 {  // one input spectrum -> up to 9 output spectra
 struct XArgsN {  // up to 9 input spectra -> one output spectrum
   const void *in[9];
   void *out;
-  MultSet mult;
+  XPlan plan;
   const void *amp;
   double kf;
 };
 
-// x pass, case "one to many": X = FFT_x(in); out_o = IFFT_x(h_o X), o < count.
+// x pass, case "one to many": X = FFT_x(in); out_o = IFFT_x(h_o X), o < count,
+// one inverse transform per part X_p (out_o = C_o IFFT_x(X_p X)).
 // Shared memory holds the transformed input (kept) and one work tile.
 template <typename T, int N, int B, int NT, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) k_x_1toM(XArgs1 a, const cx<T> *__restrict__ tw) {
@@ -402,22 +446,29 @@ __global__ void __launch_bounds__(NT, MINB) k_x_1toM(XArgs1 a, const cx<T> *__re
   const int c = threadIdx.x % B, colg = col0 + c;
   ColMode<T> cm;
   cm.init(colg / H, colg % H, N, (T)a.kf);
-  for (int o = 0; o < a.mult.count; ++o) {
-    const bool use_amp = (a.mult.m[o].flags & M_AMP) != 0;
+  const ModeK<T> mcol = cm.at(0);  // k_y, k_z of this thread's column
+  for (int p = 0; p < a.plan.nparts; ++p) {
+    const MultDesc &xm = a.plan.xpart[p];
+    const bool use_amp = (xm.flags & M_AMP) != 0;
     for (int ix = threadIdx.x / B; ix < N; ix += NT / B) {
       const int e = ix * B + c;
       const T amp = use_amp ? reinterpret_cast<const T *>(a.amp)[(int64_t)ix * astride + colg] : T(0);
-      buf[e] = apply_mult<T, C>(a.mult.m[o], xin[e], cm.at(ix), amp);
+      buf[e] = apply_mult<T, C>(xm, xin[e], cm.at(ix), amp);
     }
     __syncthreads();
     smem_fft<C, N, B, B, NT, +1>(buf, tw, 1);
-    C *dst = reinterpret_cast<C *>(a.out[o]) + col0;
-    for (int e = threadIdx.x; e < N * B; e += NT) dst[(e / B) * astride + e % B] = buf[e];
+    for (int o = 0; o < a.plan.count; ++o) {
+      if (a.plan.part_of[o] != p) continue;
+      const C f = apply_mult<T, C>(a.plan.col[o], mkc<C>(T(1), T(0)), mcol, T(0));
+      C *dst = reinterpret_cast<C *>(a.out[o]) + col0;
+      for (int e = threadIdx.x; e < N * B; e += NT) dst[(e / B) * astride + e % B] = cmul(f, buf[e]);
+    }
     __syncthreads();
   }
 }
 
-// x pass, case "many to one": out = IFFT_x( sum_i h_i FFT_x(in_i) ).
+// x pass, case "many to one": out = IFFT_x( sum_i h_i FFT_x(in_i) ), one
+// forward transform per part: sum_p X_p FFT_x(sum_{i in p} C_i in_i).
 // Shared memory holds one work tile and the accumulator.
 template <typename T, int N, int B, int NT, int MINB = 1>
 __global__ void __launch_bounds__(NT, MINB) k_x_Mto1(XArgsN a, const cx<T> *__restrict__ tw) {
@@ -433,18 +484,32 @@ __global__ void __launch_bounds__(NT, MINB) k_x_Mto1(XArgsN a, const cx<T> *__re
   const int c = threadIdx.x % B, colg = col0 + c;
   ColMode<T> cm;
   cm.init(colg / H, colg % H, N, (T)a.kf);
-  for (int i = 0; i < a.mult.count; ++i) {
-    const C *src = reinterpret_cast<const C *>(a.in[i]) + col0;
-    gather_tile<N * B / NT, NT, C>([&](int e) { return src[(e / B) * astride + e % B]; },
-                                   [&](int e, C v) { buf[e] = v; });
+  const ModeK<T> mcol = cm.at(0);  // k_y, k_z of this thread's column
+  for (int p = 0; p < a.plan.nparts; ++p) {
+    // the tile loads of one input are the thread's own elements (column c),
+    // so the part's inputs accumulate without a barrier between them
+    bool first = true;
+    for (int i = 0; i < a.plan.count; ++i) {
+      if (a.plan.part_of[i] != p) continue;
+      const C f = apply_mult<T, C>(a.plan.col[i], mkc<C>(T(1), T(0)), mcol, T(0));
+      const C *src = reinterpret_cast<const C *>(a.in[i]) + col0;
+      if (first)
+        gather_tile<N * B / NT, NT, C>([&](int e) { return src[(e / B) * astride + e % B]; },
+                                       [&](int e, C v) { buf[e] = cmul(f, v); });
+      else
+        gather_tile<N * B / NT, NT, C>([&](int e) { return src[(e / B) * astride + e % B]; },
+                                       [&](int e, C v) { buf[e] = cadd(buf[e], cmul(f, v)); });
+      first = false;
+    }
     __syncthreads();
     smem_fft<C, N, B, B, NT, -1>(buf, tw, 1);
-    const bool use_amp = (a.mult.m[i].flags & M_AMP) != 0;
+    const MultDesc &xm = a.plan.xpart[p];
+    const bool use_amp = (xm.flags & M_AMP) != 0;
     for (int ix = threadIdx.x / B; ix < N; ix += NT / B) {
       const int e = ix * B + c;
       const T amp = use_amp ? reinterpret_cast<const T *>(a.amp)[(int64_t)ix * astride + colg] : T(0);
-      const C h = apply_mult<T, C>(a.mult.m[i], buf[e], cm.at(ix), amp);
-      acc[e] = i ? cadd(acc[e], h) : h;
+      const C h = apply_mult<T, C>(xm, buf[e], cm.at(ix), amp);
+      acc[e] = p ? cadd(acc[e], h) : h;
     }
     __syncthreads();
   }

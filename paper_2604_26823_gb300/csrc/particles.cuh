@@ -762,8 +762,11 @@ __global__ void k_lc_join(Geo g, T *__restrict__ xbar, T *__restrict__ pbar, con
 
 // Adjoint gather at x_k: xbar += grad_u sum W (c_k pbar . Phi_k + rhobar);
 // then (if drift != 0) pbar += drift * xbar and the running max of |cnext pbar|.
+// The FP32 kernel is capped at 40 registers (6 blocks of 256 per SM): it is
+// bound by the latency of its dependent corner loads, and more resident warps
+// keep more of them in flight.
 template <typename T>
-__global__ void k_adj_gather(Geo g, const T *__restrict__ x, const V4<T> *__restrict__ phi,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1) k_adj_gather(Geo g, const T *__restrict__ x, const V4<T> *__restrict__ phi,
                              const T *__restrict__ rhobar, T ck, T *__restrict__ xbar, T *__restrict__ pbar,
                              T drift, T cnext, unsigned long long *maxslot) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
