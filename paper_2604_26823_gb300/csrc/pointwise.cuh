@@ -166,26 +166,29 @@ __device__ __forceinline__ void bias_rate(const LossParams &lp, T delta, T onep,
 
 // Per cell: delta = rho - 1 from the fixed-point density, the likelihood term
 // (block partials in FP64), dbar = lw * d(term)/d delta (+ cot), delta_out.
+// Each thread walks its cells four at a time, all loads of the four first:
+// the grid is fixed (it fixes the summation order), so the loads of several
+// cells must be in flight per thread.  The terms are added in cell order, as
+// one cell at a time would add them.
 template <typename T>
 __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const int *fx_exp,
                        const T *__restrict__ data, const T *__restrict__ resp, const T *__restrict__ cot,
                        T *__restrict__ dbar, T *__restrict__ delta_out, int64_t n, double *partial) {
   const int e = -__ldg(fx_exp);
   SumAcc<T> acc;  // the likelihood terms, each formed in T
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  auto cell = [&](int64_t i, long long q, T d, T r, T cv) {
     // delta = rho - 1 formed in integers (one unit weight is 2^-e) and
     // 1 + delta = rho, each rounded once from the exact fixed-point value, so
     // both keep full relative precision (delta near 0, rho near the floor)
     T delta, onep;
     if constexpr (sizeof(T) == 4) {
-      delta = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
-      onep = scalbnf(fx_i64_to_f32(rho[i]), e);
+      delta = scalbnf(fx_i64_to_f32(q - (1ll << -e)), e);
+      onep = scalbnf(fx_i64_to_f32(q), e);
     } else {
-      delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
-      onep = scalbn(__ll2double_rn(rho[i]), e);
+      delta = scalbn(__ll2double_rn(q - (1ll << -e)), e);
+      onep = scalbn(__ll2double_rn(q), e);
     }
     if (delta_out) delta_out[i] = delta;
-    const T r = resp[i];
     T g = T(0);
     if (lp.lik == 0) {
       // residual of the biased field: b delta, or nbar g(delta)
@@ -196,19 +199,36 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
         f = (T)lp.nbar * gb;
         df = (T)lp.nbar * dgb;
       }
-      const T res = f - data[i];
+      const T res = f - d;
       acc.add(T(0.5) * r * res * res * (T)lp.inv_s2);
       g = r * df * res * (T)lp.inv_s2;
     } else if (r > T(0)) {
       T gb, dgb;
       bias_rate(lp, delta, onep, gb, dgb);
       const T lam = r * (T)lp.nbar * gb;
-      const T cnt = data[i];
-      acc.add(lam - cnt * log(lam));
-      g = r * (T)lp.nbar * dgb * (T(1) - cnt / lam);
+      acc.add(lam - d * log(lam));
+      g = r * (T)lp.nbar * dgb * (T(1) - d / lam);
     }
-    if (dbar) dbar[i] = (T)lp.lw * g + (cot ? cot[i] : T(0));
+    if (dbar) dbar[i] = (T)lp.lw * g + cv;
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int U = 4;
+  for (; i + (U - 1) * stride < n; i += U * stride) {
+    long long q[U];
+    T d[U], r[U], cv[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int64_t k = i + j * stride;
+      q[j] = rho[k];
+      d[j] = data[k];
+      r[j] = resp[k];
+      cv[j] = cot ? cot[k] : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) cell(i + j * stride, q[j], d[j], r[j], cv[j]);
   }
+  for (; i < n; i += stride) cell(i, rho[i], data[i], resp[i], cot ? cot[i] : T(0));
   block_sum_store(acc.value(), partial);
 }
 
