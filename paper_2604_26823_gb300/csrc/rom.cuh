@@ -126,14 +126,27 @@ __global__ void k_real_assign(const K *__restrict__ keys, const unsigned int *__
 
 // Fourier mode selection: canonical member of its conjugate pair, not its
 // own conjugate, |k| >= k_min; bin = floor(|k| / (sqrt(3) k_Nyq) * nbins).
+// Integer arithmetic only per mode (the FP64 unit of this GPU is narrow): the
+// test |k| >= k_min is n2 >= n2_min, the first |n|^2 at which the FP64
+// expression kf sqrt(n2) >= kmin holds (it is monotone in n2), found once on
+// the host by that same expression.
 struct ModeSel {
   int n, h, nbins;
   double kf, kmin;
+  long long n2_min;
+  void init_threshold() {
+    long long lo = 0, hi = 3ll * n * n + 1;  // kf sqrt(hi) exceeds any k_min the plan uses
+    while (lo < hi) {
+      const long long mid = (lo + hi) / 2;
+      if (kf * std::sqrt((double)mid) < kmin) lo = mid + 1;
+      else hi = mid;
+    }
+    n2_min = lo;
+  }
   __host__ __device__ int bin_of(int ix, int iy, int iz) const {
     const int nx = ix < n / 2 ? ix : ix - n;
     const int ny = iy < n / 2 ? iy : iy - n;
-    const double kk = kf * sqrt((double)(nx * nx + ny * ny + iz * iz));
-    if (kk < kmin) return -1;
+    if ((long long)nx * nx + (long long)ny * ny + (long long)iz * iz < n2_min) return -1;
     if (iz == 0 || iz == n / 2) {
       const int px = (n - ix) % n, py = (n - iy) % n;
       const long long self = (long long)ix * n + iy, part = (long long)px * n + py;
@@ -143,7 +156,7 @@ struct ModeSel {
     // integers: the largest b with 3 n^2 b^2 <= 4 nbins^2 |n|^2
     const long long n2 = (long long)nx * nx + (long long)ny * ny + (long long)iz * iz;
     const long long lhs = 4ll * nbins * nbins * n2, c = 3ll * n * n;
-    long long b = (long long)(sqrt((double)lhs / (double)c));
+    long long b = (long long)sqrtf((float)lhs / (float)c);  // estimate, corrected below
     while (b > 0 && c * b * b > lhs) --b;
     while (c * (b + 1) * (b + 1) <= lhs) ++b;
     return b < nbins - 1 ? (int)b : nbins - 1;
@@ -209,6 +222,7 @@ template <typename T> struct Rom {
     m.nbins = 100;
     m.kf = E.kf;
     m.kmin = 0.1;
+    m.init_threshold();
     return m;
   }
 
