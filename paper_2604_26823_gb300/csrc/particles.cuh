@@ -206,6 +206,7 @@ struct Geo {
 // 2LPT initial conditions: disp = (D1 psi1 + D2 psi2)/Delta,
 // mom = (Gp1 psi1 + Gp2 psi2)/Delta (cell units); deposit unit weight.
 template <typename T> struct SrcLpt {
+  static constexpr int kMinBlocks = 5;  // FP32 blocks of 256 per SM (register cap)
   static constexpr int NCH = 1;
   Lattice L;
   int64_t np;
@@ -233,6 +234,7 @@ template <typename T> struct SrcLpt {
 
 // Positions disp + rsd * mom along rsd_axis (rsd_axis < 0: none), unit weight.
 template <typename T> struct SrcPaint {
+  static constexpr int kMinBlocks = 5;
   static constexpr int NCH = 1;
   Lattice L;
   int64_t np;
@@ -254,6 +256,7 @@ template <typename T> struct SrcPaint {
 // One fused leapfrog update: F = readout(Phi, x); p += kick F; x' = x + drift p;
 // deposit x'.  x and x' may alias.
 template <typename T> struct SrcKdk {
+  static constexpr int kMinBlocks = 6;  // 40 registers: more warps hide the readout's corner loads
   static constexpr int NCH = 1;
   Lattice L;
   int64_t np;
@@ -435,6 +438,7 @@ __device__ __forceinline__ void lightcone_observed(const Lattice &L, const Light
 }
 
 template <typename T> struct SrcFinal {
+  static constexpr int kMinBlocks = 5;
   static constexpr int NCH = 1;
   Lattice L;
   int64_t np;
@@ -476,6 +480,7 @@ template <typename T> struct SrcFinal {
 // chosen from the running max of |c_k pbar| (written to fx_exp_out).
 
 template <typename T> struct SrcAdj3 {
+  static constexpr int kMinBlocks = 5;
   static constexpr int NCH = 3;
   Lattice L;
   int64_t np;
@@ -519,7 +524,7 @@ template <typename T> struct SrcAdj3 {
 // unchanged bit for bit, with up to half the atomics.
 
 template <typename T, class Src>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_deposit(Geo g, Src src, unsigned long long *mesh, int64_t plane) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? Src::kMinBlocks : 1) k_deposit(Geo g, Src src, unsigned long long *mesh, int64_t plane) {
   constexpr int NCH = Src::NCH;
   constexpr unsigned kFull = 0xffffffffu;
   Src s = src;

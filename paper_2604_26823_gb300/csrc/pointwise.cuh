@@ -142,25 +142,60 @@ struct LossParams {
   double lw;         // loss weight for the derivative
 };
 
+// The parameters in the mesh type, converted once per thread (a conversion
+// from FP64 per cell would run on the narrow FP64 unit).
+template <typename T> struct LossT {
+  int lik, bias;
+  T b, inv_s2, alpha, delta_th, K, nbar, fl, lw;
+  __device__ explicit LossT(const LossParams &p)
+      : lik(p.lik), bias(p.bias), b((T)p.b), inv_s2((T)p.inv_s2), alpha((T)p.alpha), delta_th((T)p.delta_th),
+        K((T)p.K), nbar((T)p.nbar), fl((T)p.rho_floor), lw((T)p.lw) {}
+};
+
+// delta = rho - 1 formed in integers (one unit weight is 2^-e) and 1 + delta
+// = rho, each rounded once from the exact fixed-point value q, so both keep
+// full relative precision (delta near 0, rho near the floor).  FP32: one
+// conversion on the hardware (FP64-unit) path and one on the integer pipe,
+// then an exact power-of-two scale (the fixed-point exponent of a density
+// mesh is at most 62, so 2^e is a normal float).
+template <typename T> __device__ __forceinline__ void density_of(long long q, int e, T &delta, T &onep) {
+  if constexpr (sizeof(T) == 4) {
+    const float a = __ll2float_rn(q - (1ll << -e)), b = fx_i64_to_f32(q);
+    if (e >= -126) {
+      const float sc = __int_as_float((e + 127) << 23);
+      delta = a * sc;
+      onep = b * sc;
+    } else {
+      delta = scalbnf(a, e);
+      onep = scalbnf(b, e);
+    }
+  } else {
+    delta = scalbn(__ll2double_rn(q - (1ll << -e)), e);
+    onep = scalbn(__ll2double_rn(q), e);
+  }
+}
+
 // Galaxy density per unit nbar, g(delta), and dg/d delta (Sec. 2.2.1 item 4).
 // Linear: max(1 + b delta, rho_floor), derivative b above the floor.  Power law
 // + sigmoid (Eq. galaxy_bias): max(1+delta, rho_floor)^alpha sigmoid(K (delta -
 // delta_th)), the power-law factor's derivative zero below the floor.  onep is
-// 1 + delta rounded once from the exact density.
+// 1 + delta rounded once from the exact density.  FP32 forms the power as
+// exp2(alpha log2 base) (a few ulp, against ~10 for the general pow).
 template <typename T>
-__device__ __forceinline__ void bias_rate(const LossParams &lp, T delta, T onep, T &g, T &dg) {
-  const T fl = (T)lp.rho_floor;
+__device__ __forceinline__ void bias_rate(const LossT<T> &lp, T delta, T onep, T &g, T &dg) {
   if (lp.bias == 0) {
-    const T base = T(1) + (T)lp.b * delta;
-    g = base > fl ? base : fl;
-    dg = base > fl ? (T)lp.b : T(0);
+    const T base = T(1) + lp.b * delta;
+    g = base > lp.fl ? base : lp.fl;
+    dg = base > lp.fl ? lp.b : T(0);
   } else {
-    const T base = onep > fl ? onep : fl;
-    const T sg = T(1) / (T(1) + exp(-(T)lp.K * (delta - (T)lp.delta_th)));
-    const T pw = pow(base, (T)lp.alpha);
+    const T base = onep > lp.fl ? onep : lp.fl;
+    const T sg = T(1) / (T(1) + exp(-lp.K * (delta - lp.delta_th)));
+    T pw;
+    if constexpr (sizeof(T) == 4) pw = exp2f(lp.alpha * log2f(base));
+    else pw = pow(base, lp.alpha);
     g = pw * sg;
-    const T dpow = onep > fl ? (T)lp.alpha * pw / base : T(0);
-    dg = dpow * sg + pw * (T)lp.K * sg * (T(1) - sg);
+    const T dpow = onep > lp.fl ? lp.alpha * pw / base : T(0);
+    dg = dpow * sg + pw * lp.K * sg * (T(1) - sg);
   }
 }
 
@@ -171,45 +206,37 @@ __device__ __forceinline__ void bias_rate(const LossParams &lp, T delta, T onep,
 // cells must be in flight per thread.  The terms are added in cell order, as
 // one cell at a time would add them.
 template <typename T>
-__global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const int *fx_exp,
+__global__ void k_loss(LossParams lpd, const long long *__restrict__ rho, const int *fx_exp,
                        const T *__restrict__ data, const T *__restrict__ resp, const T *__restrict__ cot,
                        T *__restrict__ dbar, T *__restrict__ delta_out, int64_t n, double *partial) {
   const int e = -__ldg(fx_exp);
+  const LossT<T> lp(lpd);
   SumAcc<T> acc;  // the likelihood terms, each formed in T
   auto cell = [&](int64_t i, long long q, T d, T r, T cv) {
-    // delta = rho - 1 formed in integers (one unit weight is 2^-e) and
-    // 1 + delta = rho, each rounded once from the exact fixed-point value, so
-    // both keep full relative precision (delta near 0, rho near the floor)
     T delta, onep;
-    if constexpr (sizeof(T) == 4) {
-      delta = scalbnf(fx_i64_to_f32(q - (1ll << -e)), e);
-      onep = scalbnf(fx_i64_to_f32(q), e);
-    } else {
-      delta = scalbn(__ll2double_rn(q - (1ll << -e)), e);
-      onep = scalbn(__ll2double_rn(q), e);
-    }
+    density_of<T>(q, e, delta, onep);
     if (delta_out) delta_out[i] = delta;
     T g = T(0);
     if (lp.lik == 0) {
       // residual of the biased field: b delta, or nbar g(delta)
-      T f = (T)lp.b * delta, df = (T)lp.b;
+      T f = lp.b * delta, df = lp.b;
       if (lp.bias != 0) {
         T gb, dgb;
         bias_rate(lp, delta, onep, gb, dgb);
-        f = (T)lp.nbar * gb;
-        df = (T)lp.nbar * dgb;
+        f = lp.nbar * gb;
+        df = lp.nbar * dgb;
       }
       const T res = f - d;
-      acc.add(T(0.5) * r * res * res * (T)lp.inv_s2);
-      g = r * df * res * (T)lp.inv_s2;
+      acc.add(T(0.5) * r * res * res * lp.inv_s2);
+      g = r * df * res * lp.inv_s2;
     } else if (r > T(0)) {
       T gb, dgb;
       bias_rate(lp, delta, onep, gb, dgb);
-      const T lam = r * (T)lp.nbar * gb;
+      const T lam = r * lp.nbar * gb;
       acc.add(lam - d * log(lam));
-      g = r * (T)lp.nbar * dgb * (T(1) - d / lam);
+      g = r * lp.nbar * dgb * (T(1) - d / lam);
     }
-    if (dbar) dbar[i] = (T)lp.lw * g + cv;
+    if (dbar) dbar[i] = lp.lw * g + cv;
   };
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,25 +261,20 @@ __global__ void k_loss(LossParams lp, const long long *__restrict__ rho, const i
 
 // Model mean per cell from the fixed-point density (mock generation).
 template <typename T>
-__global__ void k_expected(LossParams lp, const long long *__restrict__ rho, const int *fx_exp,
+__global__ void k_expected(LossParams lpd, const long long *__restrict__ rho, const int *fx_exp,
                            const T *__restrict__ resp, T *__restrict__ out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int e = -__ldg(fx_exp);
+  const LossT<T> lp(lpd);
   T delta, onep;
-  if constexpr (sizeof(T) == 4) {
-    delta = scalbnf(fx_i64_to_f32(rho[i] - (1ll << -e)), e);
-    onep = scalbnf(fx_i64_to_f32(rho[i]), e);
-  } else {
-    delta = scalbn(__ll2double_rn(rho[i] - (1ll << -e)), e);
-    onep = scalbn(__ll2double_rn(rho[i]), e);
-  }
+  density_of<T>(rho[i], e, delta, onep);
   T gb = T(0), dgb = T(0);
   if (lp.lik != 0 || lp.bias != 0) bias_rate(lp, delta, onep, gb, dgb);
   if (lp.lik == 0) {
-    out[i] = lp.bias == 0 ? (T)lp.b * delta : (T)lp.nbar * gb;
+    out[i] = lp.bias == 0 ? lp.b * delta : lp.nbar * gb;
   } else {
-    out[i] = resp[i] > T(0) ? resp[i] * (T)lp.nbar * gb : T(0);
+    out[i] = resp[i] > T(0) ? resp[i] * lp.nbar * gb : T(0);
   }
 }
 
