@@ -3,7 +3,12 @@ likelihood, the launch configuration bench.py times), checked through
 properties that hold at any size -- the FP64 oracle cannot evaluate a 256^3
 gradient in test time:
   * FP32 path vs the all-FP64 GPU path: loss and density within 1e-5, the
-    gradient's cosine >= 0.99999 and relative L2 < 4.7e-4 (1.5 x measured);
+    gradient's cosine >= 0.99999 and its relative L2 within 1.5 x the
+    largest error of two FP64 evaluations from inputs perturbed so that their
+    trajectory deviates by the FP32 path's own final-displacement error (the
+    FP32 error is set by the few particles whose CIC derivative branch flips,
+    a random quantity: measured 3.4e-4 .. 8.5e-4 over four seeds, and
+    2.8e-4 .. 1.9e-3 for such perturbed FP64 evaluations);
   * the FP64 path's gradient against its own central differences along
     seeded random directions (eps = 1e-3);
   * bit-identical repeated evaluation, and bit-identical gradients with
@@ -55,9 +60,27 @@ def test_fp32_vs_fp64_at_full_size(setup):
     print(f"256^3 FP32 vs FP64 path: loss {abs(l32 - l64) / abs(l64):.2e}, density "
           f"{np.linalg.norm(d32 - d64) / np.linalg.norm(d64):.2e}, gradient rel L2 {err:.3e} cos {cos:.9f}")
     assert cos > 0.99999
-    # measured 3.10e-4 .. 3.17e-4 on a GB300 (the CIC face crossings of the
-    # FP32 trajectory, as in test_gpu_model's FP32 bound); 1.5 x that
-    assert err < 4.7e-4
+    # the FP32-level error of this seed: FP64 evaluations whose trajectory
+    # deviates by the FP32 path's own final-displacement error
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    dd = lambda x, dt: torch.tensor(x, dtype=dt, device="cuda")
+    plan64 = api.Plan(bench.config(api, setup["nbar"], "f64"), setup["lnk"], setup["lnp"])
+    s0 = setup["s0"].astype(np.float64)
+    x64 = api.pm_evolve(plan64, dd(s0, torch.float64))[0].cpu().numpy()
+    x32 = api.pm_evolve(setup["plan32"], dd(s0, torch.float32))[0].double().cpu().numpy()
+    traj = rel(x32, x64)
+    levels = []
+    for k in range(2):
+        xi = np.random.default_rng(200 + k).standard_normal(s0.shape)
+        e0 = rel(api.pm_evolve(plan64, dd(s0 + 1e-6 * xi, torch.float64))[0].cpu().numpy(), x64)
+        amp = 1e-6 * traj / e0
+        _, _, gp = _eval(api, plan64, s0 + amp * xi, setup["counts"], setup["R"], torch.float64)
+        levels.append(rel(gp, g64))
+    del plan64
+    bound = 1.5 * max(max(levels), 1e-4)
+    print(f"256^3 FP32 final displacement rel L2 {traj:.3e}; trajectory-matched FP64 evaluations: "
+          + ", ".join(f"{v:.3e}" for v in levels) + f"; bound {bound:.3e}")
+    assert err < bound, (err, bound)
 
 
 def test_fp64_gradient_against_finite_differences(setup):
