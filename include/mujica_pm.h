@@ -275,12 +275,12 @@ pm_status pm_coarsen(int32_t n, int32_t factor, int32_t precision, int32_t mean,
  * method's inputs read once and outputs written once, meshes and particle
  * arrays as FP32 / FP64 words) and (impl_bytes_total, nullable) the bytes of
  * the implementation's own arrays (64-bit fixed-point meshes, the padded
- * force mesh, binning words) and (flops_total, nullable) the floating-point
+ * force mesh) and (flops_total, nullable) the floating-point
  * operations of the FFT passes (5 L log2 L per complex FFT of length L, half
  * for a real one; 0 for the other classes) (synchronises).
  * Classes: 0 fused readout+kick+drift+paint, 1 z-pass r2c, 2 column pass,
- * 3 x-pass with multipliers, 4 z-pass c2r, 5 adjoint 3-channel paint
- * (with its tile binning), 6 adjoint gather, 7 likelihood. */
+ * 3 x-pass with multipliers, 4 z-pass c2r, 5 adjoint 3-channel paint,
+ * 6 adjoint gather, 7 likelihood. */
 pm_status pm_profile(pm_plan *plan, int32_t enable, int32_t capacity);
 pm_status pm_profile_read(pm_plan *plan, int32_t kernel_class, double *ms_total, int64_t *launches,
                           double *bytes_total, double *impl_bytes_total, double *flops_total);
