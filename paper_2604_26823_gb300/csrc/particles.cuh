@@ -520,8 +520,12 @@ template <typename T> struct SrcAdj3 {
 // and the z cell above (the usual case away from shell crossing), its four
 // lower-z deposits land on this lane's four upper-z nodes; they are passed
 // down by a shuffle and added here, so that lane issues only its upper-z
-// atomics.  The merged sums are sums of the same integers, so the mesh is
-// unchanged bit for bit, with up to half the atomics.
+// atomics.  Same-cell merge: in each run of consecutive lanes whose particles
+// share a cell (clustered states), the lanes at even positions of the run add
+// all eight deposits of the next lane, which issues none (pairs only, so no
+// lane waits on a chain).  The merged sums are sums of the same integers, so
+// the mesh is unchanged bit for bit, with fewer atomics: the L2's reductions,
+// not their width, bound the paint.
 
 template <typename T, class Src>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? Src::kMinBlocks : 1) k_deposit(Geo g, Src src, unsigned long long *mesh, int64_t plane) {
@@ -540,6 +544,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? Src::kMinBlocks : 1) k_d
   const int uz = __shfl_down_sync(kFull, cz, 1);
   const bool merge_up = live && lane < 31 && ux == cx && uy == cy && uz == ((cz + 1) & mask);
   const bool merged_down = __shfl_up_sync(kFull, merge_up ? 1 : 0, 1) != 0 && lane > 0;
+  // same-cell pairs: in each run of lanes with one cell, the lanes at even
+  // positions take over all deposits of the next lane (no chains)
+  const bool same_next = live && lane < 31 && ux == cx && uy == cy && uz == cz;
+  const bool same_prev = __shfl_up_sync(kFull, same_next ? 1 : 0, 1) != 0 && lane > 0;
+  const unsigned starts = __ballot_sync(kFull, live && !same_prev);
+  const int run0 = 31 - __clz(starts & ((2u << lane) - 1u));
+  const bool absorber = same_next && !((lane - run0) & 1);
+  const bool absorbed = __shfl_up_sync(kFull, absorber ? 1 : 0, 1) != 0 && lane > 0;
   const T wx[2] = {T(1) - c.f[0], c.f[0]};
   const T wy[2] = {T(1) - c.f[1], c.f[1]};
   const T wz[2] = {T(1) - c.f[2], c.f[2]};
@@ -556,9 +568,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? Src::kMinBlocks : 1) k_d
         long long q1 = live ? fx_round<T>(wxy * wz[1]) : 0;
         const long long up0 = __shfl_down_sync(kFull, q0, 1);
         if (merge_up) q1 += up0;
-        if (live) {
+        const long long up1 = __shfl_down_sync(kFull, q1, 1);
+        long long qz0 = merged_down ? 0 : q0;
+        if (absorber) {
+          qz0 += up0;
+          q1 += up1;
+        }
+        if (live && !absorbed) {
           unsigned long long *col = mesh + ch * plane + ((((int64_t)xs[ox]) << g.L.logn | ys[oy]) << g.L.logn);
-          if (q0 && !merged_down) fx_add(col + cz, q0);
+          if (qz0) fx_add(col + cz, qz0);
           if (q1) fx_add(col + z1, q1);
         }
       }
